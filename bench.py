@@ -1,0 +1,409 @@
+"""Benchmark: row-wise SpGEMM C = A*A on GB300, GFLOPS = 2 x intermediate
+products / second (the paper's metric, Sec. 6), with the HBM-roofline fraction
+of the dominant kernel, the CPU oracle as a baseline and an end-to-end number
+through the host-buffer C ABI call.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--impl ours|reference] [--no-e2e] [--no-cpu-baseline]
+
+Default workload: R-MAT n = 2^20, average degree 16 (a=.57, b=c=.19), seed 1,
+float64 values uniform in [-1, 1] (about 2.09e10 products, 9.7e9 entries in C,
+which needs an int64 row pointer). A step is one whole SpGEMM: n_prod, both
+binning steps, symbolic, scan, C allocation and numeric. Inputs are resident
+in HBM when the timed region starts; A (193 MB) is larger than L2 and every
+step writes about 116 GB of C, so nothing stays L2-resident between steps.
+
+Under torchrun (N > 1) each rank computes a contiguous slab of C's rows
+(split by A's non-zeros); value = all products / the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "SpGEMM GFLOPS (2x intermediate products/s)"
+
+WORKLOADS = {
+    "rmat20": ("C = A*A, A = R-MAT n=2^20, degree 16 (a=.57,b=.19,c=.19), seed 1, "
+               "float64 U[-1,1]", lambda: W.rmat(20, 16, seed=1)),
+    "stencil27_128": ("C = A*A, A = 27-point stencil on 128^3, off-diagonal U[0.5,1.5], "
+                      "diagonal 27, seed 3", lambda: W.stencil27(128, seed=3)),
+    "laplace2d_64": ("C = A*A, A = 5-point Laplacian on 64x64 (4 / -1)",
+                     lambda: W.laplacian_2d(64)),
+    "rmat18": ("C = A*A, A = R-MAT n=2^18, degree 16, seed 1 (small profiling case)",
+               lambda: W.rmat(18, 16, seed=1)),
+}
+
+SLOT_NAMES = ([f"sym_bin{j}" for j in range(16)] + [f"num_bin{j}" for j in range(16)]
+              + ["nprod", "sym_pass1", "sym_pass2", "num_pass1", "num_pass2", "scan"])
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def row_slab(A, rank, ws):
+    """Contiguous rows of C for this rank, split evenly by A's non-zeros."""
+    if ws == 1:
+        return 0, A.rows
+    rpt = A.rpt.astype(np.int64)
+    cuts = [0] + [int(np.searchsorted(rpt, rpt[-1] * r // ws)) for r in range(1, ws)] + [A.rows]
+    cuts = [min(max(c, 0), A.rows) for c in cuts]
+    for r in range(1, len(cuts)):
+        cuts[r] = max(cuts[r], cuts[r - 1])
+    return cuts[rank], cuts[rank + 1]
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4:]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        pmax = max(r[2] for r in rows)
+        load = [r for r in rows if r[2] >= 0.5 * pmax] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in load for i, v in enumerate(r[3][1:5])
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(load),
+                "power_w_max": pmax}
+
+
+def compulsory_bytes(A, r0, r1, nnzC):
+    """Bytes a row window of C = A*A must move at least (the roofline model):
+    A's rows, the distinct B (= A) rows they reference, and C."""
+    rpt = A.rpt.astype(np.int64)
+    a_bytes = 4 * (r1 - r0 + 1) + 12 * int(rpt[r1] - rpt[r0])
+    ks = np.unique(A.col[rpt[r0]:rpt[r1]])
+    lens = rpt[ks + 1] - rpt[ks]
+    b_bytes = 8 * ks.size + 12 * int(lens.sum())
+    c_bytes = 8 * (r1 - r0 + 1) + 12 * int(nnzC)
+    return a_bytes + b_bytes + c_bytes, b_bytes
+
+
+def cpu_baseline(A, target_products=1.5e9):
+    """The oracle as it stands, on a strided row sample of the same workload."""
+    import oracle
+    nprod = oracle.nprod(A, A)
+    total = int(nprod.sum())
+    stride = max(1, int(np.ceil(total / target_products)))
+    rows = np.arange(0, A.rows, stride)
+    rpt = A.rpt.astype(np.int64)
+    lens = rpt[rows + 1] - rpt[rows]
+    srpt = np.zeros(rows.size + 1, dtype=np.int64)
+    np.cumsum(lens, out=srpt[1:])
+    idx = np.concatenate([np.arange(rpt[r], rpt[r + 1]) for r in rows]) if rows.size else np.zeros(0, np.int64)
+    As = W.Csr(rows.size, A.cols, srpt, A.col[idx], A.val[idx])
+    sprod = int(nprod[rows].sum())
+    threads = oracle.max_threads()
+    t = time.perf_counter()
+    oracle.spgemm(As, A, threads=threads, with_abs=False)
+    dt = time.perf_counter() - t
+    return {"value": round(2.0 * sprod / dt / 1e9, 4), "unit": "GFLOPS", "cores": threads,
+            "kind": "oracle", "seconds": round(dt, 3),
+            "sample": f"every {stride}th row of A ({rows.size} rows, {sprod} products, "
+                      f"{sprod / total:.3f} of the workload); full two-phase oracle (count, "
+                      f"dense-accumulator multiply, sort) on {threads} threads"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    desc, gen = WORKLOADS[args.workload]
+    A = gen()
+    import oracle
+    vals = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        info = cpu_baseline(A, target_products=args.ref_products)
+        if i >= args.warmup:
+            vals.append(info["value"])
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GFLOPS",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(info["seconds"] * 1000, 2), "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GFLOPS", "cores": info["cores"],
+                             "kind": "oracle", "sample": info["sample"]},
+            "e2e": {"value": round(v, 4), "unit": "GFLOPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-products", type=float, default=1.5e9)
+    ap.add_argument("--config", default=None, help="bin configuration JSON file")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and not os.environ.get("BENCH_ALLOW_SHORT"):
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2206_07244_gb300 as ops
+    from paper_2206_07244_gb300 import _abi
+
+    desc, gen = WORKLOADS[args.workload]
+    A = gen()
+    r0, r1 = row_slab(A, rank, ws)
+    dA = ops.CSR.from_workload(A, device=f"cuda:{local}")
+    cfg = json.load(open(args.config)) if args.config else None
+    h = ops.Handle(cfg)
+    lib = _abi.lib()
+    import ctypes
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step():
+        h.symbolic(dA, dA, r0, r1)
+        C = h.numeric(dA, dA)
+        return C
+
+    for _ in range(args.warmup):
+        C = step()
+        del C
+    h.status()
+    stats = h.stats()
+    nnzC_slab = stats["total_nnz"]
+    nprod_slab = stats["total_nprod"]
+
+    _abi.check(lib.spgemm_set_timing(h._h, 1), "spgemm_set_timing")
+    ms_arr = (ctypes.c_double * 38)()
+    ln_arr = (ctypes.c_int64 * 38)()
+    _abi.check(lib.spgemm_kernel_times(h._h, ms_arr, ln_arr, 38, 1), "spgemm_kernel_times")
+
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            C = step()
+            del C
+        ev1.record(stream)
+        barrier()
+    h.status()
+    ms = ev0.elapsed_time(ev1)
+    _abi.check(lib.spgemm_kernel_times(h._h, ms_arr, ln_arr, 38, 1), "spgemm_kernel_times")
+    lib.spgemm_set_timing(h._h, 0)
+    kms = list(ms_arr)
+    kln = list(ln_arr)
+    ms_max = ms
+    nprod_all = nprod_slab
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        p = torch.tensor([nprod_slab], dtype=torch.int64, device="cuda")
+        dist.all_reduce(p)
+        nprod_all = int(p.item())
+    value = 2.0 * nprod_all * args.steps / (ms_max / 1e3) / 1e9
+
+    # dominant kernel and its roofline
+    k = int(np.argmax(kms))
+    bins_sym = (ctypes.c_int64 * 48)()
+    bins_num = (ctypes.c_int64 * 48)()
+    lib.spgemm_bin_stats(h._h, 0, bins_sym, 48)
+    lib.spgemm_bin_stats(h._h, 1, bins_num, 48)
+    rpt64 = A.rpt.astype(np.int64)
+    total_bytes, b_bytes = compulsory_bytes(A, r0, r1, nnzC_slab)
+    if k < 32:
+        phase, j = divmod(k, 16)
+        bs = list(bins_num if phase else bins_sym)
+        rows_j, size_j, nnza_j = bs[j], bs[16 + j], bs[32 + j]
+        a_b = 8 * rows_j + 12 * nnza_j
+        out_b = (16 * rows_j + 12 * size_j) if phase else 16 * rows_j
+        algo = a_b + b_bytes + out_b
+        algo_desc = (f"{'numeric' if phase else 'symbolic'} bin {j}: {rows_j} rows, "
+                     f"{nnza_j} A entries, {'n_nz' if phase else 'n_prod'} {size_j}; bytes = A rows "
+                     f"(12/entry + 8/row) + referenced B rows + "
+                     f"{'C rows (12/entry + 16/row)' if phase else 'n_nz out (16/row)'}")
+    else:
+        algo = total_bytes
+        algo_desc = "whole product (A + referenced B + C)"
+    launches = max(kln[k], 1)
+    avg_ms = kms[k] / launches
+    peak, peak_kind = peaks()
+    achieved = algo / (avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": SLOT_NAMES[k], "achieved": round(achieved, 2),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
+                "algorithmic_bytes_per_launch": int(algo), "avg_launch_ms": round(avg_ms, 4),
+                "bytes_model": algo_desc}
+    whole = {"bytes_per_step": int(total_bytes),
+             "achieved_gbs": round(total_bytes / (ms / args.steps / 1e3) / 1e9, 2),
+             "frac": round(total_bytes / (ms / args.steps / 1e3) / 1e9 / peak, 4)}
+    breakdown = {SLOT_NAMES[i]: round(kms[i] / args.steps, 3) for i in range(len(kms)) if kms[i] > 0}
+    gpu_launches = int(sum(kln) + kln[37])   # the scan slot covers two kernels
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        e2e = run_e2e(A, lib, args.e2e_steps, nprod_slab if ws == 1 else None)
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and ws == 1:
+        cpu = cpu_baseline(A)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "GFLOPS", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": desc, "rows": A.rows, "nnzA": A.nnz,
+                           "nprod": nprod_all, "nnzC": nnzC_slab if ws == 1 else None,
+                           "cache": "inputs larger than L2 (A 193 MB for rmat20; each step "
+                                    "writes C, far larger than L2)",
+                           "parallelism": f"row slabs x{ws}" if ws > 1 else "single GPU",
+                           "bin_config": "autotuned" if args.config else "default"},
+                "roofline": roofline, "roofline_whole_step": whole,
+                "stage_ms_per_step": breakdown,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(A, lib, steps, nprod):
+    """The same multiply through spgemm_multiply_host: A from pinned host
+    memory, C streamed back chunk by chunk into pinned host buffers."""
+    import ctypes
+
+    import torch
+
+    import paper_2206_07244_gb300 as ops
+    from paper_2206_07244_gb300 import _abi
+    rpt = torch.from_numpy(A.rpt).pin_memory()
+    col = torch.from_numpy(A.col).pin_memory()
+    val = torch.from_numpy(A.val).pin_memory()
+    a = _abi.CsrIn()
+    a.rows, a.cols, a.nnz = A.rows, A.cols, A.nnz
+    a.rpt, a.rpt_is_i64 = rpt.data_ptr(), 0
+    a.col, a.val = col.data_ptr(), val.data_ptr()
+    SINK = _abi.SINK_FN
+    got = {"nnz": 0, "chunks": 0}
+
+    def sink(ctx, r0, rows, prpt, pcol, pval, n):
+        got["nnz"] += n
+        got["chunks"] += 1
+        return 0
+
+    cb = SINK(sink)
+    h = ops.Handle()
+    nnz = ctypes.c_int64()
+    chunk = 1 << 30
+    # one untimed call allocates the pinned staging buffers
+    _abi.check(lib.spgemm_multiply_host(h._h, ctypes.byref(a), ctypes.byref(a), chunk, cb, None,
+                                        ctypes.byref(nnz)), "spgemm_multiply_host")
+    if nprod is None:
+        nprod = h.stats()["total_nprod"]
+    times = []
+    for _ in range(steps):
+        got["nnz"] = 0
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _abi.check(lib.spgemm_multiply_host(h._h, ctypes.byref(a), ctypes.byref(a), chunk, cb,
+                                            None, ctypes.byref(nnz)), "spgemm_multiply_host")
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+    h.close()
+    assert got["nnz"] == nnz.value
+    t = float(np.mean(times))
+    h2d = 4 * (A.rows + 1) + 12 * A.nnz
+    d2h = 8 * (A.rows + 1) + 12 * int(nnz.value)
+    return {"value": round(2.0 * nprod / t / 1e9, 3), "unit": "GFLOPS", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "seconds_per_step": round(t, 4), "steps": steps,
+            "chunks": got["chunks"], "call": "spgemm_multiply_host (pinned host A in, C streamed "
+                                              "back in 1 GiB chunks)"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

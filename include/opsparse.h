@@ -1,0 +1,208 @@
+/*
+ * opsparse.h - C ABI of the GB300 (sm_103a) row-wise SpGEMM library.
+ *
+ * The library computes C = A * B for sparse A (M x K) and B (K x N) in CSR
+ * form, row by row (Gustavson's row-wise dataflow, Eq. 2, Sec. 2.1), as a
+ * two-phase method (Sec. 2.2): a symbolic phase counts the non-zeros of each
+ * output row, C is allocated from the total, and a numeric phase writes each
+ * row's sorted column indices and values.
+ *
+ * Conventions for every entry point:
+ *   - Pointers inside spgemm_csr_in / spgemm_csr_out are DEVICE pointers on
+ *     the handle's device unless a function says otherwise.
+ *   - Integers: column indices int32; input row pointers int32 or int64
+ *     (rpt_is_i64); the output row pointer is always int64 (an output row
+ *     window may hold more than 2^31 - 1 entries).
+ *   - Values are IEEE float64 (the paper evaluates in double precision,
+ *     Sec. 6).
+ *   - Every call is ordered on the handle's CUDA stream. Calls that must
+ *     return a count to the host (spgemm_symbolic) synchronise that stream;
+ *     the others only enqueue work.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ *   - Return value: SPGEMM_OK (0) or one of the negative codes below;
+ *     spgemm_strerror() names them. On error no output is handed over and
+ *     the handle stays usable unless the code is SPGEMM_ERR_CUDA.
+ */
+#ifndef OPSPARSE_H
+#define OPSPARSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPGEMM_OK                  0
+#define SPGEMM_ERR_INVALID        -1  /* bad argument or malformed CSR      */
+#define SPGEMM_ERR_SHAPE          -2  /* A.cols != B.rows                   */
+#define SPGEMM_ERR_OOM            -3  /* an allocation failed               */
+#define SPGEMM_ERR_STATE          -4  /* call out of order (numeric before symbolic) */
+#define SPGEMM_ERR_TIMEOUT        -5  /* a bounded device wait ran out      */
+#define SPGEMM_ERR_CUDA           -6  /* a CUDA runtime call failed         */
+#define SPGEMM_ERR_INTERNAL       -7  /* a device-side check failed (table overflow) */
+#define SPGEMM_ERR_ABORTED        -8  /* a host sink callback asked to stop  */
+
+#define SPGEMM_MAX_BINS 16
+
+/* Read-only CSR input (Sec. 2.1.1): rpt has rows+1 entries, col/val have
+ * nnz = rpt[rows] entries. Columns inside a row need not be sorted and may
+ * repeat; repeated (row, col) pairs are summed. Caller-owned device memory. */
+typedef struct {
+    int64_t rows, cols, nnz;
+    const void *rpt;
+    int32_t rpt_is_i64;          /* 0: int32 row pointers, 1: int64 */
+    const int32_t *col;
+    const double *val;           /* may be NULL for spgemm_symbolic */
+} spgemm_csr_in;
+
+/* CSR output written by the library: rows = row window length, cols = B.cols,
+ * nnz = number of stored entries; rpt (int64, rows+1) starts at 0 for the
+ * first row of the window; columns ascending and unique in every row.
+ * Ownership of rpt/col/val passes to the caller (see spgemm_alloc_fn). */
+typedef struct {
+    int64_t rows, cols, nnz;
+    int64_t *rpt;
+    int32_t *col;
+    double *val;
+} spgemm_csr_out;
+
+/* Device-memory allocator hooks. alloc returns a device pointer aligned to at
+ * least 256 bytes or NULL; free releases it. `stream` is the cudaStream_t of
+ * the handle, passed as void*. With both NULL the library uses a private
+ * stream-ordered pool (cudaMallocAsync); output arrays then belong to the
+ * caller, who releases them with spgemm_free(). */
+typedef void *(*spgemm_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*spgemm_free_fn)(void *ptr, void *stream, void *ctx);
+
+/* Bin configuration (Sec. 5.1, Sec. 5.6, Sec. 5.7). Bin j of a phase takes
+ * the rows whose size (n_prod for the symbolic phase, n_nz for the numeric
+ * phase) is <= range[j] and > range[j-1] (Algorithm 1: first j with
+ * size <= r_range[j]); the last used bin must have range -1 (no bound).
+ * kernel[j] picks the kernel that computes bin j from the table printed by
+ * spgemm_kernel_info(); its capacity must hold range[j]. nbins = 0 in a
+ * phase selects the library's defaults for this device.
+ * lanes_per_brow: threads that walk one row of B together (1..32, a power
+ * of two), or 0 to pick it per output row from the mean referenced B-row
+ * length. */
+typedef struct {
+    int32_t sym_nbins;
+    int32_t sym_kernel[SPGEMM_MAX_BINS];
+    int64_t sym_range[SPGEMM_MAX_BINS];
+    int32_t num_nbins;
+    int32_t num_kernel[SPGEMM_MAX_BINS];
+    int64_t num_range[SPGEMM_MAX_BINS];
+    int32_t lanes_per_brow;
+    int32_t reserved[7];
+} spgemm_config;
+
+typedef struct spgemm_handle spgemm_handle;
+
+/* Create a handle on the current CUDA device. cfg NULL = defaults; stream is
+ * a cudaStream_t (NULL = legacy default stream). Creates the handle's side
+ * streams (Sec. 5: bins of one phase run concurrently) and a small pinned
+ * host buffer. */
+int spgemm_create(spgemm_handle **h, const spgemm_config *cfg,
+                  spgemm_alloc_fn alloc, spgemm_free_fn free_fn, void *ctx,
+                  void *stream);
+
+/* Replace the bin configuration (validated; SPGEMM_ERR_INVALID if a range
+ * exceeds its kernel's capacity or the last range is bounded). */
+int spgemm_set_config(spgemm_handle *h, const spgemm_config *cfg);
+int spgemm_get_config(const spgemm_handle *h, spgemm_config *cfg);
+
+/* Symbolic phase for output rows [row_begin, row_end) of C = A * B
+ * (Sec. 5 steps 1-4): per-row intermediate-product count n_prod (Sec. 2.1.2)
+ * written into C.rpt, symbolic binning (Algorithms 1-3), per-bin symbolic
+ * kernels (Algorithm 4; large rows use a shared-memory column bitmap), and
+ * the first numeric binning pass, which yields the total. Allocates the
+ * output row pointer (row_end - row_begin + 1 int64) and keeps it in the
+ * handle until spgemm_numeric. *nnzC receives the number of entries of the
+ * window. A.val/B.val are not read. Synchronises the handle's stream. */
+int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A,
+                    const spgemm_csr_in *B, int64_t row_begin, int64_t row_end,
+                    int64_t *nnzC);
+
+/* Numeric phase for the window of the last spgemm_symbolic (Sec. 5 steps
+ * 4-6): second numeric binning pass, in-place exclusive scan of C.rpt
+ * (Sec. 5.3), allocation of C.col/C.val overlapped with those kernels
+ * (Sec. 5.4), then per-bin numeric kernels (Algorithm 5 hash, condense,
+ * sort; large rows use the bitmap-rank kernel). If C->col and C->val are
+ * non-NULL on entry they are used as the output buffers (each must hold
+ * *nnzC entries); otherwise they are allocated. On return C describes the
+ * window and owns rpt/col/val. Does not synchronise. */
+int spgemm_numeric(spgemm_handle *h, const spgemm_csr_in *A,
+                   const spgemm_csr_in *B, spgemm_csr_out *C);
+
+/* spgemm_symbolic over all rows followed by spgemm_numeric. */
+int spgemm_multiply(spgemm_handle *h, const spgemm_csr_in *A,
+                    const spgemm_csr_in *B, spgemm_csr_out *C);
+
+/* Wait for the handle's stream and report device-side checks raised by any
+ * earlier call (a full hash table, a row whose numeric size differs from its
+ * symbolic count): SPGEMM_OK or SPGEMM_ERR_INTERNAL (the check is then
+ * cleared). */
+int spgemm_status(spgemm_handle *h);
+
+/* Release memory that the library allocated for an output when no allocator
+ * hooks were given (stream-ordered on the handle's stream). */
+int spgemm_free(spgemm_handle *h, void *ptr);
+
+/* Free the handle's scratch memory, streams and host buffers. Never frees
+ * an output handed to the caller. */
+int spgemm_destroy(spgemm_handle *h);
+
+/* Receives one chunk of C rows copied back to host memory:
+ * rows [row_begin, row_begin + rows), rpt points at rows+1 int64 offsets
+ * (absolute: rpt[k] - rpt[0] indexes col/val), col/val hold nnz entries.
+ * All pointers are host memory owned by the library and valid only during
+ * the call. Return 0 to continue, nonzero to stop (SPGEMM_ERR_ABORTED). */
+typedef int (*spgemm_host_sink_fn)(void *ctx, int64_t row_begin, int64_t rows,
+                                   const int64_t *rpt, const int32_t *col,
+                                   const double *val, int64_t nnz);
+
+/* C = A * B for operands in HOST memory (pinned memory gives full copy
+ * speed): copies A and B to the device (once if A and B are the same
+ * arrays), runs spgemm_multiply, then streams C back in chunks of at most
+ * chunk_bytes of (col, val) through two pinned staging buffers, calling
+ * sink for each chunk in row order while the next chunk is in flight. C
+ * never has to fit in host memory. *nnzC (may be NULL) receives the total.
+ * Device copies and C are released before returning. */
+int spgemm_multiply_host(spgemm_handle *h, const spgemm_csr_in *A,
+                         const spgemm_csr_in *B, int64_t chunk_bytes,
+                         spgemm_host_sink_fn sink, void *ctx, int64_t *nnzC);
+
+/* Per-bin statistics of the last symbolic call for phase 0 (symbolic bins)
+ * or 1 (numeric bins): 3 * SPGEMM_MAX_BINS int64: rows per bin, sum of the
+ * row sizes per bin (n_prod or n_nz), A entries of the bin's rows. */
+int spgemm_bin_stats(const spgemm_handle *h, int phase, int64_t *out, int n);
+
+/* Per-kernel timing with CUDA events recorded on the stream each kernel is
+ * launched on. spgemm_kernel_times synchronises the handle's stream and
+ * returns accumulated milliseconds and launch counts per slot: slots 0-15
+ * the symbolic bins, 16-31 the numeric bins, 32 n_prod, 33/34 symbolic
+ * binning passes 1/2, 35/36 numeric binning passes 1/2, 37 the scan
+ * (38 slots). reset != 0 clears the totals. */
+int spgemm_set_timing(spgemm_handle *h, int enable);
+int spgemm_kernel_times(spgemm_handle *h, double *ms, int64_t *launches, int n,
+                        int reset);
+
+/* Per-phase statistics of the last symbolic/numeric call: 4 + 2 * NB
+ * int64 values: total n_prod, max row n_prod, total n_nz, max row n_nz,
+ * then the symbolic and numeric bin sizes (SPGEMM_MAX_BINS each). */
+int spgemm_last_stats(const spgemm_handle *h, int64_t *out, int n);
+
+/* Describe kernel `id` of a phase (0 symbolic, 1 numeric): its threads per
+ * row, threads per block, table capacity (entries; for the bitmap kernel
+ * the number of columns one pass covers) and the largest row size it
+ * accepts. Returns SPGEMM_ERR_INVALID past the last kernel. */
+int spgemm_kernel_info(int phase, int id, int32_t *threads_per_row,
+                       int32_t *block, int64_t *table, int64_t *max_size);
+
+const char *spgemm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OPSPARSE_H */

@@ -1,0 +1,807 @@
+// Host orchestration and the C ABI (include/opsparse.h).
+//
+// One call of the plain path follows the paper's six steps (Sec. 5):
+//   1 setup     C.rpt allocated; n_prod per row computed into it; scratch
+//               reserved while that kernel runs (Sec. 5.4).
+//   2 binning   Algorithm 1 on n_prod, one 16-word device->host read of the
+//               bin sizes, Algorithm 2 (or the identity order of Algorithm 3
+//               when one bin holds every row).
+//   3 symbolic  one kernel per non-empty bin, largest rows first, each on its
+//               own stream so small-row kernels fill SMs around the large
+//               ones (Sec. 5.5); n_nz overwrites n_prod in C.rpt.
+//   4 binning   Algorithm 1 on n_nz gives the total; one device->host read.
+//   5 numeric   Algorithm 2 on n_nz, in-place exclusive scan of C.rpt,
+//               C.col / C.val allocated after those kernels are queued
+//               (Sec. 5.4), one numeric kernel per bin, largest first.
+//   6 cleanup   scratch is kept in the handle for the next call; nothing is
+//               freed between launches (Sec. 5.5).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+#include "opsparse.h"
+
+using namespace ops;
+
+namespace {
+
+constexpr int kSide = 8;              // side streams for concurrent bin kernels
+constexpr size_t kCountersBytes = 2048;  // 2 x Counters + the error word
+
+// Event-timing slots: 0..15 symbolic bins, 16..31 numeric bins, then the
+// setup/binning/scan kernels.
+enum Slot {
+    kSlotSymBin = 0,
+    kSlotNumBin = 16,
+    kSlotNprod = 32,
+    kSlotSymPass1 = 33,
+    kSlotSymPass2 = 34,
+    kSlotNumPass1 = 35,
+    kSlotNumPass2 = 36,
+    kSlotScan = 37,
+    kSlots = 38,
+};
+
+}  // namespace
+
+struct spgemm_handle {
+    int device = 0;
+    int sm_count = 0;
+    int smem_dyn_max = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_side[kSide] = {};
+    spgemm_alloc_fn alloc = nullptr;
+    spgemm_free_fn freefn = nullptr;
+    void *ctx = nullptr;
+    cudaMemPool_t pool = nullptr;
+    spgemm_config cfg{};
+    // scratch arena: [Counters sym | Counters num | err] [bins] [tile sums]
+    unsigned char *arena = nullptr;
+    size_t arena_bytes = 0;
+    Counters *h_cnt = nullptr;  // pinned, 2 entries
+    // state between symbolic and numeric
+    int state = 0;
+    int64_t row0 = 0, mw = 0, ncols = 0, nnz = 0;
+    int64_t *crpt = nullptr;
+    long long num_size[kMaxBins] = {};
+    int64_t stats[4 + 2 * SPGEMM_MAX_BINS] = {};
+    int64_t bin_stats[2][3 * SPGEMM_MAX_BINS] = {};
+    // per-kernel CUDA-event timing (off unless requested)
+    // pinned staging for spgemm_multiply_host
+    unsigned char *stage = nullptr;
+    size_t stage_bytes = 0;
+    int64_t *stage_rpt = nullptr;
+    size_t stage_rpt_n = 0;
+    bool timing = false;
+    cudaEvent_t t0[kSlots] = {}, t1[kSlots] = {};
+    bool pending[kSlots] = {};
+    double ms[kSlots] = {};
+    long long launches[kSlots] = {};
+};
+
+namespace {
+
+void *dev_alloc(spgemm_handle *h, size_t bytes) {
+    bytes = std::max<size_t>(bytes, 256);
+    if (h->alloc) return h->alloc(bytes, h->stream, h->ctx);
+    void *p = nullptr;
+    if (cudaMallocFromPoolAsync(&p, bytes, h->pool, h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(spgemm_handle *h, void *p) {
+    if (!p) return;
+    if (h->freefn) h->freefn(p, h->stream, h->ctx);
+    else cudaFreeAsync(p, h->stream);
+}
+
+void flush_slot(spgemm_handle *h, int k) {
+    if (!h->pending[k]) return;
+    cudaEventSynchronize(h->t1[k]);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->t0[k], h->t1[k]) == cudaSuccess) h->ms[k] += ms;
+    cudaGetLastError();
+    h->pending[k] = false;
+}
+
+void time_begin(spgemm_handle *h, int k, cudaStream_t s) {
+    if (!h->timing) return;
+    flush_slot(h, k);
+    cudaEventRecord(h->t0[k], s);
+}
+
+void time_end(spgemm_handle *h, int k, cudaStream_t s) {
+    if (!h->timing) return;
+    cudaEventRecord(h->t1[k], s);
+    h->pending[k] = true;
+    h->launches[k] += 1;
+}
+
+Counters *d_counters(spgemm_handle *h, int phase) {
+    return reinterpret_cast<Counters *>(h->arena) + phase;
+}
+
+int *d_err(spgemm_handle *h) {
+    return reinterpret_cast<int *>(h->arena + 2 * sizeof(Counters));
+}
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+int ensure_arena(spgemm_handle *h, int64_t mw) {
+    const int64_t ntiles = (mw + bin_tile_rows() - 1) / bin_tile_rows();
+    const size_t need = kCountersBytes + align256(sizeof(int32_t) * (size_t)std::max<int64_t>(mw, 1)) +
+                        align256(sizeof(long long) * (size_t)(ntiles + 2));
+    if (h->arena && h->arena_bytes >= need) return SPGEMM_OK;
+    int keep_err = 0;
+    if (h->arena) {
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SPGEMM_ERR_CUDA;
+        cudaMemcpy(&keep_err, d_err(h), sizeof(int), cudaMemcpyDeviceToHost);
+        dev_free(h, h->arena);
+        h->arena = nullptr;
+        h->arena_bytes = 0;
+    }
+    const size_t bytes = need + need / 4;
+    h->arena = static_cast<unsigned char *>(dev_alloc(h, bytes));
+    if (!h->arena) return SPGEMM_ERR_OOM;
+    h->arena_bytes = bytes;
+    if (cudaMemsetAsync(h->arena, 0, kCountersBytes, h->stream) != cudaSuccess) return SPGEMM_ERR_CUDA;
+    if (keep_err &&
+        cudaMemcpyAsync(d_err(h), &keep_err, sizeof(int), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        return SPGEMM_ERR_CUDA;
+    return SPGEMM_OK;
+}
+
+int32_t *d_bins(spgemm_handle *h) {
+    return reinterpret_cast<int32_t *>(h->arena + kCountersBytes);
+}
+
+long long *d_tiles(spgemm_handle *h) {
+    return reinterpret_cast<long long *>(h->arena + kCountersBytes +
+                                         align256(sizeof(int32_t) * (size_t)std::max<int64_t>(h->mw, 1)));
+}
+
+bool is_pow2_lanes(int x) { return x == 0 || x == 1 || x == 2 || x == 4 || x == 8 || x == 16 || x == 32; }
+
+int validate_config(const spgemm_config &c) {
+    if (!is_pow2_lanes(c.lanes_per_brow)) return SPGEMM_ERR_INVALID;
+    for (int phase = 0; phase < 2; ++phase) {
+        const int nb = phase ? c.num_nbins : c.sym_nbins;
+        const int32_t *k = phase ? c.num_kernel : c.sym_kernel;
+        const int64_t *r = phase ? c.num_range : c.sym_range;
+        const int nk = phase ? num_kernel_count() : sym_kernel_count();
+        if (nb < 1 || nb > SPGEMM_MAX_BINS) return SPGEMM_ERR_INVALID;
+        for (int j = 0; j < nb; ++j) {
+            if (k[j] < 0 || k[j] >= nk) return SPGEMM_ERR_INVALID;
+            const KernelDesc &d = phase ? num_kernel(k[j]) : sym_kernel(k[j]);
+            const bool last = j == nb - 1;
+            if (last != (r[j] < 0)) return SPGEMM_ERR_INVALID;      // only the last bin is unbounded
+            if (last) {
+                if (!d.bitmap) return SPGEMM_ERR_INVALID;          // it must take any row size
+            } else {
+                if (r[j] > d.max_size) return SPGEMM_ERR_INVALID;
+                if (j > 0 && r[j] <= r[j - 1]) return SPGEMM_ERR_INVALID;
+            }
+        }
+    }
+    return SPGEMM_OK;
+}
+
+void default_config(spgemm_config &c) {
+    std::memset(&c, 0, sizeof(c));
+    // Symbolic: every table at least 1.2x the largest n_prod of its bin
+    // (Sec. 5.7, the paper's choice "Sym_1.2x"); the bitmap takes the rest.
+    const int ns = sym_kernel_count();
+    c.sym_nbins = ns;
+    for (int j = 0; j < ns; ++j) {
+        c.sym_kernel[j] = j;
+        const KernelDesc &d = sym_kernel(j);
+        c.sym_range[j] = d.bitmap ? -1 : static_cast<int64_t>(d.table * 5 / 6);
+    }
+    // Numeric: every table at least 2x the largest n_nz of its bin (Sec. 5.7,
+    // "Num_2x").
+    const int nn = num_kernel_count();
+    c.num_nbins = nn;
+    for (int j = 0; j < nn; ++j) {
+        c.num_kernel[j] = j;
+        const KernelDesc &d = num_kernel(j);
+        c.num_range[j] = d.bitmap ? -1 : static_cast<int64_t>(d.table / 2);
+    }
+    c.lanes_per_brow = 0;
+}
+
+int cuda_rc(cudaError_t e) {
+    if (e == cudaSuccess) return SPGEMM_OK;
+    if (e == cudaErrorMemoryAllocation) return SPGEMM_ERR_OOM;
+    return SPGEMM_ERR_CUDA;
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_rc(e_); \
+    } while (0)
+
+int check_csr_in(const spgemm_csr_in *m) {
+    if (!m || m->rows < 0 || m->cols < 0 || m->nnz < 0 || !m->rpt) return SPGEMM_ERR_INVALID;
+    if (m->nnz > 0 && !m->col) return SPGEMM_ERR_INVALID;
+    if (m->cols > INT32_MAX || m->rows > INT32_MAX) return SPGEMM_ERR_INVALID;
+    if (!m->rpt_is_i64 && m->nnz > INT32_MAX) return SPGEMM_ERR_INVALID;
+    return SPGEMM_OK;
+}
+
+Operands make_operands(const spgemm_csr_in *A, const spgemm_csr_in *B, int64_t r0, int64_t mw) {
+    Operands op;
+    op.arpt = A->rpt; op.a64 = A->rpt_is_i64 ? 1 : 0; op.acol = A->col; op.aval = A->val;
+    op.brpt = B->rpt; op.b64 = B->rpt_is_i64 ? 1 : 0; op.bcol = B->col; op.bval = B->val;
+    op.row0 = r0; op.mw = mw; op.ncols = B->cols;
+    return op;
+}
+
+// Launch the kernels of one phase, one per non-empty bin, largest rows first,
+// spread over the side streams.
+int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *size,
+             const long long *offset, bool identity, int64_t *crpt, int32_t *ccol, double *cval) {
+    const int nb = phase ? h->cfg.num_nbins : h->cfg.sym_nbins;
+    const int32_t *kid = phase ? h->cfg.num_kernel : h->cfg.sym_kernel;
+    CK(cudaEventRecord(h->ev_fork, h->stream));
+    int used = 0;
+    for (int j = nb - 1; j >= 0; --j) {
+        if (size[j] <= 0) continue;
+        cudaStream_t s = h->side[used % kSide];
+        if (used < kSide) CK(cudaStreamWaitEvent(s, h->ev_fork, 0));
+        BinWork w;
+        w.bins = identity ? nullptr : d_bins(h);
+        w.off = identity ? 0 : offset[j];
+        w.cnt = size[j];
+        w.crpt = crpt; w.ccol = ccol; w.cval = cval;
+        w.lanes = h->cfg.lanes_per_brow;
+        w.err = d_err(h);
+        const KernelDesc &d = phase ? num_kernel(kid[j]) : sym_kernel(kid[j]);
+        size_t smem = 0;
+        if (d.bitmap) {
+            if (phase == 0) {
+                const int64_t words = std::min<int64_t>((op.ncols + 31) / 32, h->smem_dyn_max / 4);
+                smem = static_cast<size_t>(std::max<int64_t>(words, 1)) * 4;
+            } else {
+                const int64_t words = std::min<int64_t>((op.ncols + 63) / 64, h->smem_dyn_max / 12);
+                smem = static_cast<size_t>(std::max<int64_t>(words, 1)) * 12;
+            }
+        }
+        const int slot = (phase ? kSlotNumBin : kSlotSymBin) + j;
+        time_begin(h, slot, s);
+        CK(phase ? launch_num(kid[j], op, w, smem, s) : launch_sym(kid[j], op, w, smem, s));
+        time_end(h, slot, s);
+        ++used;
+    }
+    for (int i = 0; i < std::min(used, kSide); ++i) {
+        CK(cudaEventRecord(h->ev_side[i], h->side[i]));
+        CK(cudaStreamWaitEvent(h->stream, h->ev_side[i], 0));
+    }
+    return SPGEMM_OK;
+}
+
+// Bin sizes -> (offsets, identity?) : identity when one bin holds every row
+// (the generalisation of Algorithm 3: no scatter pass, rows in index order).
+bool plan_bins(const Counters &c, int nb, long long *size, long long *offset) {
+    long long acc = 0;
+    int nonempty = 0;
+    for (int j = 0; j < nb; ++j) {
+        size[j] = static_cast<long long>(c.bin_cnt[j]);
+        offset[j] = acc;
+        acc += size[j];
+        nonempty += size[j] > 0;
+    }
+    return nonempty <= 1;
+}
+
+int read_counters(spgemm_handle *h) {
+    CK(cudaMemcpyAsync(h->h_cnt, h->arena, 2 * sizeof(Counters) + sizeof(int),
+                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const int err = *reinterpret_cast<const int *>(reinterpret_cast<const unsigned char *>(h->h_cnt) +
+                                                   2 * sizeof(Counters));
+    for (int phase = 0; phase < 2; ++phase)
+        for (int j = 0; j < SPGEMM_MAX_BINS; ++j) {
+            h->bin_stats[phase][j] = static_cast<int64_t>(h->h_cnt[phase].bin_cnt[j]);
+            h->bin_stats[phase][SPGEMM_MAX_BINS + j] = static_cast<int64_t>(h->h_cnt[phase].bin_sum[j]);
+            h->bin_stats[phase][2 * SPGEMM_MAX_BINS + j] = static_cast<int64_t>(h->h_cnt[phase].bin_nnza[j]);
+        }
+    return err ? SPGEMM_ERR_INTERNAL : SPGEMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *spgemm_strerror(int code) {
+    switch (code) {
+        case SPGEMM_OK: return "ok";
+        case SPGEMM_ERR_INVALID: return "invalid argument";
+        case SPGEMM_ERR_SHAPE: return "shape mismatch (A.cols != B.rows)";
+        case SPGEMM_ERR_OOM: return "out of device memory";
+        case SPGEMM_ERR_STATE: return "call out of order";
+        case SPGEMM_ERR_TIMEOUT: return "bounded device wait expired";
+        case SPGEMM_ERR_CUDA: return "CUDA runtime error";
+        case SPGEMM_ERR_INTERNAL: return "device-side check failed";
+        case SPGEMM_ERR_ABORTED: return "the host sink stopped the transfer";
+        default: return "unknown error";
+    }
+}
+
+int spgemm_kernel_info(int phase, int id, int32_t *tpr, int32_t *block, int64_t *table,
+                       int64_t *max_size) {
+    const int n = phase ? num_kernel_count() : sym_kernel_count();
+    if (phase < 0 || phase > 1 || id < 0 || id >= n) return SPGEMM_ERR_INVALID;
+    const KernelDesc &d = phase ? num_kernel(id) : sym_kernel(id);
+    if (tpr) *tpr = d.tpr;
+    if (block) *block = d.block;
+    if (table) *table = d.table;
+    if (max_size) *max_size = d.bitmap ? -1 : d.max_size;
+    return SPGEMM_OK;
+}
+
+int spgemm_create(spgemm_handle **out, const spgemm_config *cfg, spgemm_alloc_fn alloc,
+                  spgemm_free_fn free_fn, void *ctx, void *stream) {
+    if (!out) return SPGEMM_ERR_INVALID;
+    *out = nullptr;
+    if ((alloc == nullptr) != (free_fn == nullptr)) return SPGEMM_ERR_INVALID;
+    spgemm_handle *h = new (std::nothrow) spgemm_handle();
+    if (!h) return SPGEMM_ERR_OOM;
+    int rc = SPGEMM_OK;
+    do {
+        if (cudaGetDevice(&h->device) != cudaSuccess) { rc = SPGEMM_ERR_CUDA; break; }
+        int optin = 0;
+        cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+        h->smem_dyn_max = optin - 1024;  // room for the kernels' static shared arrays
+        if (sym_prepare(h->smem_dyn_max) != cudaSuccess || num_prepare(h->smem_dyn_max) != cudaSuccess) {
+            rc = SPGEMM_ERR_CUDA;
+            break;
+        }
+        h->stream = static_cast<cudaStream_t>(stream);
+        h->alloc = alloc;
+        h->freefn = free_fn;
+        h->ctx = ctx;
+        for (int i = 0; i < kSide; ++i) {
+            if (cudaStreamCreateWithFlags(&h->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_side[i], cudaEventDisableTiming) != cudaSuccess) {
+                rc = SPGEMM_ERR_CUDA;
+                break;
+            }
+        }
+        if (rc) break;
+        if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess) { rc = SPGEMM_ERR_CUDA; break; }
+        if (cudaMallocHost(&h->h_cnt, 2 * sizeof(Counters) + 64) != cudaSuccess) { rc = SPGEMM_ERR_OOM; break; }
+        if (!alloc) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = h->device;
+            if (cudaMemPoolCreate(&h->pool, &props) != cudaSuccess) { rc = SPGEMM_ERR_CUDA; break; }
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(h->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        if (cfg) {
+            if (validate_config(*cfg) != SPGEMM_OK) { rc = SPGEMM_ERR_INVALID; break; }
+            h->cfg = *cfg;
+        } else {
+            default_config(h->cfg);
+        }
+    } while (0);
+    if (rc != SPGEMM_OK) {
+        cudaGetLastError();
+        spgemm_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return SPGEMM_OK;
+}
+
+int spgemm_set_config(spgemm_handle *h, const spgemm_config *cfg) {
+    if (!h) return SPGEMM_ERR_INVALID;
+    if (!cfg) {
+        default_config(h->cfg);
+        return SPGEMM_OK;
+    }
+    if (validate_config(*cfg) != SPGEMM_OK) return SPGEMM_ERR_INVALID;
+    h->cfg = *cfg;
+    return SPGEMM_OK;
+}
+
+int spgemm_get_config(const spgemm_handle *h, spgemm_config *cfg) {
+    if (!h || !cfg) return SPGEMM_ERR_INVALID;
+    *cfg = h->cfg;
+    return SPGEMM_OK;
+}
+
+int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in *B,
+                    int64_t row_begin, int64_t row_end, int64_t *nnzC) {
+    if (!h || !nnzC) return SPGEMM_ERR_INVALID;
+    int rc = check_csr_in(A);
+    if (rc) return rc;
+    if ((rc = check_csr_in(B))) return rc;
+    if (A->cols != B->rows) return SPGEMM_ERR_SHAPE;
+    if (row_begin < 0 || row_end < row_begin || row_end > A->rows) return SPGEMM_ERR_INVALID;
+    if (h->state == 1) {  // an earlier symbolic result was never consumed
+        dev_free(h, h->crpt);
+        h->crpt = nullptr;
+        h->state = 0;
+    }
+    const int64_t mw = row_end - row_begin;
+    h->mw = mw;
+    if ((rc = ensure_arena(h, mw))) return rc;
+    int64_t *crpt = static_cast<int64_t *>(dev_alloc(h, sizeof(int64_t) * (size_t)(mw + 1)));
+    if (!crpt) return SPGEMM_ERR_OOM;
+    auto fail = [&](int code) {
+        dev_free(h, crpt);
+        return code;
+    };
+    // zero both phases' counters, keep the error word
+    if (cudaMemsetAsync(h->arena, 0, 2 * sizeof(Counters), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(crpt, 0, sizeof(int64_t) * (size_t)(mw + 1), h->stream) != cudaSuccess)
+        return fail(SPGEMM_ERR_CUDA);
+    const Operands op = make_operands(A, B, row_begin, mw);
+    // step 1: n_prod per row into C.rpt
+    time_begin(h, kSlotNprod, h->stream);
+    if (launch_nprod(op, crpt, h->sm_count * 8, h->stream) != cudaSuccess) return fail(SPGEMM_ERR_CUDA);
+    time_end(h, kSlotNprod, h->stream);
+    // step 2: symbolic binning by n_prod
+    Ranges rs{};
+    rs.nb = h->cfg.sym_nbins;
+    for (int j = 0; j < rs.nb; ++j) rs.r[j] = h->cfg.sym_range[j];
+    time_begin(h, kSlotSymPass1, h->stream);
+    if (launch_bin_pass1(crpt, mw, rs, op, d_counters(h, 0), nullptr, h->stream) != cudaSuccess)
+        return fail(SPGEMM_ERR_CUDA);
+    time_end(h, kSlotSymPass1, h->stream);
+    if ((rc = read_counters(h))) return fail(rc);
+    long long ssize[kMaxBins] = {}, soff[kMaxBins] = {};
+    const bool sid = plan_bins(h->h_cnt[0], rs.nb, ssize, soff);
+    h->stats[0] = static_cast<int64_t>(h->h_cnt[0].total);
+    h->stats[1] = static_cast<int64_t>(h->h_cnt[0].max_size);
+    for (int j = 0; j < SPGEMM_MAX_BINS; ++j) h->stats[4 + j] = j < rs.nb ? ssize[j] : 0;
+    if (!sid) {
+        time_begin(h, kSlotSymPass2, h->stream);
+        if (launch_bin_pass2(crpt, mw, rs, soff, d_counters(h, 0), d_bins(h), h->stream) != cudaSuccess)
+            return fail(SPGEMM_ERR_CUDA);
+        time_end(h, kSlotSymPass2, h->stream);
+    }
+    // step 3: symbolic kernels, largest rows first
+    if ((rc = run_bins(h, 0, op, ssize, soff, sid, crpt, nullptr, nullptr))) return fail(rc);
+    // step 4: numeric binning pass 1 -> total n_nz (and tile sums for the scan)
+    Ranges rn{};
+    rn.nb = h->cfg.num_nbins;
+    for (int j = 0; j < rn.nb; ++j) rn.r[j] = h->cfg.num_range[j];
+    time_begin(h, kSlotNumPass1, h->stream);
+    if (launch_bin_pass1(crpt, mw, rn, op, d_counters(h, 1), d_tiles(h), h->stream) != cudaSuccess)
+        return fail(SPGEMM_ERR_CUDA);
+    time_end(h, kSlotNumPass1, h->stream);
+    if ((rc = read_counters(h))) return fail(rc);
+    h->stats[2] = static_cast<int64_t>(h->h_cnt[1].total);
+    h->stats[3] = static_cast<int64_t>(h->h_cnt[1].max_size);
+    for (int j = 0; j < SPGEMM_MAX_BINS; ++j)
+        h->stats[4 + SPGEMM_MAX_BINS + j] = j < rn.nb ? static_cast<int64_t>(h->h_cnt[1].bin_cnt[j]) : 0;
+    for (int j = 0; j < kMaxBins; ++j) h->num_size[j] = j < rn.nb ? h->h_cnt[1].bin_cnt[j] : 0;
+    h->crpt = crpt;
+    h->row0 = row_begin;
+    h->ncols = B->cols;
+    h->nnz = static_cast<int64_t>(h->h_cnt[1].total);
+    h->state = 1;
+    *nnzC = h->nnz;
+    return SPGEMM_OK;
+}
+
+int spgemm_numeric(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in *B,
+                   spgemm_csr_out *C) {
+    if (!h || !C) return SPGEMM_ERR_INVALID;
+    if (h->state != 1) return SPGEMM_ERR_STATE;
+    int rc = check_csr_in(A);
+    if (rc) return rc;
+    if ((rc = check_csr_in(B))) return rc;
+    if (A->cols != B->rows) return SPGEMM_ERR_SHAPE;
+    if (h->row0 + h->mw > A->rows || B->cols != h->ncols) return SPGEMM_ERR_STATE;
+    if ((A->nnz > 0 && !A->val) || (B->nnz > 0 && !B->val)) return SPGEMM_ERR_INVALID;
+    const bool given = C->col != nullptr && C->val != nullptr;
+    // from here on the symbolic result is consumed
+    h->state = 0;
+    int64_t *crpt = h->crpt;
+    h->crpt = nullptr;
+    const Operands op = make_operands(A, B, h->row0, h->mw);
+    const int nb = h->cfg.num_nbins;
+    long long off[kMaxBins] = {};
+    long long acc = 0;
+    int nonempty = 0;
+    for (int j = 0; j < nb; ++j) {
+        off[j] = acc;
+        acc += h->num_size[j];
+        nonempty += h->num_size[j] > 0;
+    }
+    const bool nid = nonempty <= 1;
+    Ranges rn{};
+    rn.nb = nb;
+    for (int j = 0; j < nb; ++j) rn.r[j] = h->cfg.num_range[j];
+    int32_t *ccol = C->col;
+    double *cval = C->val;
+    auto fail = [&](int code) {
+        dev_free(h, crpt);
+        if (!given) {
+            dev_free(h, ccol);
+            dev_free(h, cval);
+        }
+        return code;
+    };
+    if (!nid) {
+        time_begin(h, kSlotNumPass2, h->stream);
+        if (launch_bin_pass2(crpt, h->mw, rn, off, d_counters(h, 1), d_bins(h), h->stream) != cudaSuccess)
+            return fail(SPGEMM_ERR_CUDA);
+        time_end(h, kSlotNumPass2, h->stream);
+    }
+    time_begin(h, kSlotScan, h->stream);
+    if (launch_scan(crpt, h->mw, d_tiles(h), h->stream) != cudaSuccess) return fail(SPGEMM_ERR_CUDA);
+    time_end(h, kSlotScan, h->stream);
+    // C.col / C.val allocated while the binning and scan kernels run (Sec. 5.4)
+    if (!given) {
+        ccol = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * (size_t)h->nnz));
+        cval = static_cast<double *>(dev_alloc(h, sizeof(double) * (size_t)h->nnz));
+        if (!ccol || !cval) return fail(SPGEMM_ERR_OOM);
+    }
+    if ((rc = run_bins(h, 1, op, h->num_size, off, nid, crpt, ccol, cval))) return fail(rc);
+    C->rows = h->mw;
+    C->cols = h->ncols;
+    C->nnz = h->nnz;
+    C->rpt = crpt;
+    C->col = ccol;
+    C->val = cval;
+    return SPGEMM_OK;
+}
+
+int spgemm_multiply(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in *B,
+                    spgemm_csr_out *C) {
+    if (!h || !A || !C) return SPGEMM_ERR_INVALID;
+    int64_t nnz = 0;
+    int rc = spgemm_symbolic(h, A, B, 0, A->rows, &nnz);
+    if (rc) return rc;
+    return spgemm_numeric(h, A, B, C);
+}
+
+int spgemm_status(spgemm_handle *h) {
+    if (!h) return SPGEMM_ERR_INVALID;
+    CK(cudaStreamSynchronize(h->stream));
+    if (!h->arena) return SPGEMM_OK;
+    int err = 0;
+    CK(cudaMemcpy(&err, d_err(h), sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        CK(cudaMemset(d_err(h), 0, sizeof(int)));
+        return SPGEMM_ERR_INTERNAL;
+    }
+    return SPGEMM_OK;
+}
+
+int spgemm_free(spgemm_handle *h, void *ptr) {
+    if (!h) return SPGEMM_ERR_INVALID;
+    dev_free(h, ptr);
+    return SPGEMM_OK;
+}
+
+int spgemm_last_stats(const spgemm_handle *h, int64_t *out, int n) {
+    if (!h || !out || n < 0) return SPGEMM_ERR_INVALID;
+    const int m = std::min<int>(n, 4 + 2 * SPGEMM_MAX_BINS);
+    std::memcpy(out, h->stats, sizeof(int64_t) * (size_t)m);
+    return SPGEMM_OK;
+}
+
+int spgemm_multiply_host(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in *B,
+                         int64_t chunk_bytes, spgemm_host_sink_fn sink, void *ctx,
+                         int64_t *nnzC) {
+    if (!h || !A || !B || !sink) return SPGEMM_ERR_INVALID;
+    int rc = check_csr_in(A);
+    if (rc) return rc;
+    if ((rc = check_csr_in(B))) return rc;
+    if (A->cols != B->rows) return SPGEMM_ERR_SHAPE;
+    if ((A->nnz > 0 && !A->val) || (B->nnz > 0 && !B->val)) return SPGEMM_ERR_INVALID;
+    if (chunk_bytes < (1 << 20)) chunk_bytes = 1 << 20;
+    const bool same = A->rpt == B->rpt && A->col == B->col && A->val == B->val &&
+                      A->rows == B->rows && A->rpt_is_i64 == B->rpt_is_i64;
+    // host -> device copies of the operands
+    void *dev[6] = {};
+    auto release = [&]() {
+        for (void *p : dev) dev_free(h, p);
+    };
+    auto upload = [&](const spgemm_csr_in *m, void **slot, spgemm_csr_in *d) -> int {
+        const size_t rb = (size_t)(m->rows + 1) * (m->rpt_is_i64 ? 8 : 4);
+        slot[0] = dev_alloc(h, rb);
+        slot[1] = dev_alloc(h, sizeof(int32_t) * (size_t)m->nnz);
+        slot[2] = dev_alloc(h, sizeof(double) * (size_t)m->nnz);
+        if (!slot[0] || !slot[1] || !slot[2]) return SPGEMM_ERR_OOM;
+        CK(cudaMemcpyAsync(slot[0], m->rpt, rb, cudaMemcpyHostToDevice, h->stream));
+        if (m->nnz) {
+            CK(cudaMemcpyAsync(slot[1], m->col, sizeof(int32_t) * (size_t)m->nnz,
+                               cudaMemcpyHostToDevice, h->stream));
+            CK(cudaMemcpyAsync(slot[2], m->val, sizeof(double) * (size_t)m->nnz,
+                               cudaMemcpyHostToDevice, h->stream));
+        }
+        *d = *m;
+        d->rpt = slot[0];
+        d->col = static_cast<const int32_t *>(slot[1]);
+        d->val = static_cast<const double *>(slot[2]);
+        return SPGEMM_OK;
+    };
+    spgemm_csr_in dA{}, dB{};
+    if ((rc = upload(A, dev, &dA))) { release(); return rc; }
+    if (same) dB = dA;
+    else if ((rc = upload(B, dev + 3, &dB))) { release(); return rc; }
+    int64_t nnz = 0;
+    if ((rc = spgemm_symbolic(h, &dA, &dB, 0, A->rows, &nnz))) { release(); return rc; }
+    spgemm_csr_out C{};
+    if ((rc = spgemm_numeric(h, &dA, &dB, &C))) { release(); return rc; }
+    auto release_all = [&]() {
+        release();
+        dev_free(h, C.rpt);
+        dev_free(h, C.col);
+        dev_free(h, C.val);
+    };
+    // pinned staging: the whole row pointer plus two chunk buffers
+    const size_t nr = (size_t)C.rows + 1;
+    if (h->stage_rpt_n < nr) {
+        if (h->stage_rpt) cudaFreeHost(h->stage_rpt);
+        h->stage_rpt = nullptr;
+        h->stage_rpt_n = 0;
+        if (cudaMallocHost(&h->stage_rpt, sizeof(int64_t) * nr) != cudaSuccess) {
+            release_all();
+            return SPGEMM_ERR_OOM;
+        }
+        h->stage_rpt_n = nr;
+    }
+    if (h->stage_bytes < 2 * (size_t)chunk_bytes) {
+        if (h->stage) cudaFreeHost(h->stage);
+        h->stage = nullptr;
+        h->stage_bytes = 0;
+        if (cudaMallocHost(&h->stage, 2 * (size_t)chunk_bytes) != cudaSuccess) {
+            release_all();
+            return SPGEMM_ERR_OOM;
+        }
+        h->stage_bytes = 2 * (size_t)chunk_bytes;
+    }
+    if (cudaMemcpyAsync(h->stage_rpt, C.rpt, sizeof(int64_t) * nr, cudaMemcpyDeviceToHost, h->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        release_all();
+        return SPGEMM_ERR_CUDA;
+    }
+    const int64_t *rpt = h->stage_rpt;
+    // rows per chunk: as many as fit in chunk_bytes of (col, val), at least one
+    struct Chunk { int64_t r0, r1; };
+    auto next_chunk = [&](int64_t r0) {
+        int64_t r1 = r0 + 1;
+        int64_t lo = r0 + 1, hi = C.rows;
+        while (lo <= hi) {  // largest r1 with 12 * (rpt[r1] - rpt[r0]) <= chunk_bytes
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (12 * (rpt[mid] - rpt[r0]) <= chunk_bytes) { r1 = mid; lo = mid + 1; }
+            else hi = mid - 1;
+        }
+        return Chunk{r0, r1};
+    };
+    cudaEvent_t done[2] = {};
+    for (auto &e : done)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            release_all();
+            return SPGEMM_ERR_CUDA;
+        }
+    auto enqueue = [&](const Chunk &c, int b) -> bool {
+        const int64_t n = rpt[c.r1] - rpt[c.r0];
+        if (12 * n > chunk_bytes) return false;  // one row larger than a chunk
+        unsigned char *buf = h->stage + (size_t)b * (size_t)chunk_bytes;
+        if (n) {
+            if (cudaMemcpyAsync(buf, C.col + rpt[c.r0], sizeof(int32_t) * (size_t)n,
+                                cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+                cudaMemcpyAsync(buf + ((sizeof(int32_t) * (size_t)n + 255) & ~size_t(255)),
+                                C.val + rpt[c.r0], sizeof(double) * (size_t)n,
+                                cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+                return false;
+        }
+        return cudaEventRecord(done[b], h->stream) == cudaSuccess;
+    };
+    rc = SPGEMM_OK;
+    if (C.rows > 0) {
+        Chunk cur = next_chunk(0);
+        if (!enqueue(cur, 0)) rc = SPGEMM_ERR_INVALID;
+        int b = 0;
+        while (rc == SPGEMM_OK) {
+            Chunk nxt{cur.r1, cur.r1};
+            const bool more = cur.r1 < C.rows;
+            if (more) {
+                nxt = next_chunk(cur.r1);
+                if (!enqueue(nxt, b ^ 1)) { rc = SPGEMM_ERR_INVALID; break; }
+            }
+            if (cudaEventSynchronize(done[b]) != cudaSuccess) { rc = SPGEMM_ERR_CUDA; break; }
+            const int64_t n = rpt[cur.r1] - rpt[cur.r0];
+            unsigned char *buf = h->stage + (size_t)b * (size_t)chunk_bytes;
+            const int32_t *hc = reinterpret_cast<const int32_t *>(buf);
+            const double *hv = reinterpret_cast<const double *>(
+                buf + ((sizeof(int32_t) * (size_t)n + 255) & ~size_t(255)));
+            if (sink(ctx, cur.r0, cur.r1 - cur.r0, rpt + cur.r0, hc, hv, n) != 0) {
+                rc = SPGEMM_ERR_ABORTED;
+                break;
+            }
+            if (!more) break;
+            cur = nxt;
+            b ^= 1;
+        }
+    }
+    cudaStreamSynchronize(h->stream);
+    for (auto &e : done) cudaEventDestroy(e);
+    release_all();
+    if (rc == SPGEMM_OK && nnzC) *nnzC = nnz;
+    return rc;
+}
+
+int spgemm_bin_stats(const spgemm_handle *h, int phase, int64_t *out, int n) {
+    if (!h || !out || phase < 0 || phase > 1 || n < 0) return SPGEMM_ERR_INVALID;
+    const int m = std::min<int>(n, 3 * SPGEMM_MAX_BINS);
+    std::memcpy(out, h->bin_stats[phase], sizeof(int64_t) * (size_t)m);
+    return SPGEMM_OK;
+}
+
+int spgemm_set_timing(spgemm_handle *h, int enable) {
+    if (!h) return SPGEMM_ERR_INVALID;
+    if (enable && !h->t0[0]) {
+        for (int k = 0; k < kSlots; ++k) {
+            if (cudaEventCreate(&h->t0[k]) != cudaSuccess || cudaEventCreate(&h->t1[k]) != cudaSuccess)
+                return SPGEMM_ERR_CUDA;
+        }
+    }
+    h->timing = enable != 0;
+    return SPGEMM_OK;
+}
+
+int spgemm_kernel_times(spgemm_handle *h, double *ms, int64_t *launches, int n, int reset) {
+    if (!h || n < 0) return SPGEMM_ERR_INVALID;
+    CK(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < kSlots; ++k) {
+        if (h->t1[k]) flush_slot(h, k);
+    }
+    const int m = std::min<int>(n, kSlots);
+    for (int k = 0; k < m; ++k) {
+        if (ms) ms[k] = h->ms[k];
+        if (launches) launches[k] = h->launches[k];
+    }
+    if (reset) {
+        for (int k = 0; k < kSlots; ++k) {
+            h->ms[k] = 0.0;
+            h->launches[k] = 0;
+        }
+    }
+    return SPGEMM_OK;
+}
+
+int spgemm_destroy(spgemm_handle *h) {
+    if (!h) return SPGEMM_OK;
+    if (h->side[0]) cudaStreamSynchronize(h->stream);
+    if (h->state == 1) dev_free(h, h->crpt);
+    dev_free(h, h->arena);
+    if (h->side[0]) cudaStreamSynchronize(h->stream);
+    for (int i = 0; i < kSide; ++i) {
+        if (h->side[i]) cudaStreamDestroy(h->side[i]);
+        if (h->ev_side[i]) cudaEventDestroy(h->ev_side[i]);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    for (int k = 0; k < kSlots; ++k) {
+        if (h->t0[k]) cudaEventDestroy(h->t0[k]);
+        if (h->t1[k]) cudaEventDestroy(h->t1[k]);
+    }
+    if (h->h_cnt) cudaFreeHost(h->h_cnt);
+    if (h->stage) cudaFreeHost(h->stage);
+    if (h->stage_rpt) cudaFreeHost(h->stage_rpt);
+    if (h->pool) cudaMemPoolDestroy(h->pool);
+    delete h;
+    return SPGEMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// Device helpers shared by the SpGEMM kernels (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ops {
+
+// Device error codes written to the handle's error word (first one wins).
+enum : int {
+    DERR_NONE = 0,
+    DERR_TABLE_FULL = 1,      // a hash probe visited every slot
+    DERR_COUNT_MISMATCH = 2,  // numeric row size differs from the symbolic count
+    DERR_WINDOW = 3,          // bitmap window bookkeeping failed
+};
+
+__device__ __forceinline__ void set_error(int *err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+// Row pointer load for int32 or int64 CSR row pointers (runtime flag, uniform
+// across the grid, so the branch costs nothing measurable).
+__device__ __forceinline__ int64_t ld_rpt(const void *rpt, int is64, int64_t i) {
+    return is64 ? __ldg(static_cast<const long long *>(rpt) + i)
+                : static_cast<int64_t>(__ldg(static_cast<const int *>(rpt) + i));
+}
+
+// Hash slot of a column key in a table of T slots. The paper multiplies the
+// key by a constant and reduces modulo the table size (Sec. 5.2); here the
+// product with a Fibonacci constant is reduced by its HIGH bits (a shift for
+// a power-of-two T, a multiply-high otherwise). Low bits of stencil columns
+// repeat with the grid stride, so taking low bits would pile keys that
+// differ by a multiple of the stride onto one slot.
+constexpr uint32_t kHashMul = 0x9E3779B1u;
+
+template <int T>
+__device__ __forceinline__ uint32_t hash_slot(int key) {
+    const uint32_t x = static_cast<uint32_t>(key) * kHashMul;
+    if constexpr ((T & (T - 1)) == 0) {
+        constexpr int lg = __builtin_ctz(T);
+        return lg == 0 ? 0u : (x >> (32 - lg));
+    } else {
+        return static_cast<uint32_t>((static_cast<uint64_t>(x) * T) >> 32);
+    }
+}
+
+template <int T>
+__device__ __forceinline__ uint32_t next_slot(uint32_t h) {
+    if constexpr ((T & (T - 1)) == 0) return (h + 1) & (T - 1);
+    else return (h + 1 == static_cast<uint32_t>(T)) ? 0u : h + 1;
+}
+
+// Threads that walk one B row together: a power of two no larger than the
+// row group, chosen from the mean length of the referenced B rows unless
+// the configuration fixes it.
+__device__ __forceinline__ int pick_lanes(int fixed, int64_t nprod, int64_t nnza, int group) {
+    int cap = group < 32 ? group : 32;
+    if (fixed > 0) return fixed < cap ? fixed : cap;
+    if (nnza <= 0) return 1;
+    int64_t mean = (nprod + nnza - 1) / nnza;
+    int s = 1;
+    while (s < mean && s < cap) s <<= 1;
+    return s;
+}
+
+// --- row-group synchronisation and reductions --------------------------------
+// A row group is TPR consecutive threads. TPR <= 32: a slice of one warp;
+// TPR > 32: the whole block (one row per block).
+
+template <int TPR>
+__device__ __forceinline__ unsigned group_mask() {
+    if constexpr (TPR >= 32) return 0xffffffffu;
+    else {
+        const unsigned lane = threadIdx.x & 31u;
+        const unsigned base = lane & ~static_cast<unsigned>(TPR - 1);
+        return ((1u << TPR) - 1u) << base;
+    }
+}
+
+template <int TPR>
+__device__ __forceinline__ void group_sync() {
+    if constexpr (TPR > 32) __syncthreads();
+    else __syncwarp(group_mask<TPR>());
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_sum_xor(V v, int width) {
+    for (int o = width >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the row group; every thread of the group gets the result.
+// `red` must hold 32 values of V when TPR > 32.
+template <int TPR, typename V>
+__device__ __forceinline__ V group_sum(V v, V *red) {
+    if constexpr (TPR <= 32) {
+        return warp_sum_xor(v, TPR);
+    } else {
+        v = warp_sum_xor(v, 32);
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        __syncthreads();  // earlier readers of `red` are done
+        if (l == 0) red[w] = v;
+        __syncthreads();
+        V t = (l < (TPR >> 5)) ? red[l] : V(0);
+        return warp_sum_xor(t, 32);  // every warp forms the same total
+    }
+}
+
+// Exclusive count of `flag` over the row group in thread order, plus the
+// group total. `red` must hold 33 ints when TPR > 32.
+template <int TPR>
+__device__ __forceinline__ void group_excl_count(bool flag, int &prefix, int &total, int *red) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned bal = __ballot_sync(0xffffffffu, flag);
+    if constexpr (TPR <= 32) {
+        const unsigned gm = group_mask<TPR>();
+        const unsigned mine = bal & gm;
+        prefix = __popc(mine & ((1u << lane) - 1u));
+        total = __popc(mine);
+    } else {
+        const int w = threadIdx.x >> 5;
+        const int in_warp = __popc(bal & ((1u << lane) - 1u));
+        __syncthreads();
+        if (lane == 0) red[w] = __popc(bal);
+        __syncthreads();
+        if (w == 0) {
+            int x = (lane < (TPR >> 5)) ? red[lane] : 0;
+            int inc = x;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= static_cast<unsigned>(o)) inc += y;
+            }
+            if (lane < (TPR >> 5)) red[lane] = inc - x;
+            if (lane == 31) red[32] = inc;
+        }
+        __syncthreads();
+        prefix = red[w] + in_warp;
+        total = red[32];
+    }
+}
+
+__device__ __forceinline__ int64_t upper_bound_rpt(const void *rpt, int is64, int64_t lo,
+                                                   int64_t hi, int64_t p) {
+    // largest r in [lo, hi) with rpt[r] <= p (rpt[lo] <= p assumed)
+    while (hi - lo > 1) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        if (ld_rpt(rpt, is64, mid) <= p) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+}  // namespace ops

@@ -1,0 +1,82 @@
+// Internal interface between the host orchestration (api.cu) and the kernel
+// translation units. Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ops {
+
+constexpr int kMaxBins = 16;
+
+// Operands of one SpGEMM row window, as the kernels see them.
+struct Operands {
+    const void *arpt; int a64; const int32_t *acol; const double *aval;
+    const void *brpt; int b64; const int32_t *bcol; const double *bval;
+    int64_t row0;   // A row of window row 0
+    int64_t mw;     // rows in the window
+    int64_t ncols;  // columns of B (and C)
+};
+
+// What one bin kernel launch works on.
+struct BinWork {
+    const int32_t *bins;  // window row ids grouped by bin; nullptr = identity
+    int64_t off, cnt;     // this bin's slice of `bins`
+    int64_t *crpt;        // window C.rpt (int64, mw + 1)
+    int32_t *ccol;        // numeric only
+    double *cval;         // numeric only
+    int lanes;            // threads per B row, 0 = per-row automatic
+    int *err;             // device error word
+};
+
+struct Ranges {
+    long long r[kMaxBins];
+    int nb;
+};
+
+// Counters written by the binning passes (device memory, zeroed per call).
+struct Counters {
+    unsigned long long bin_cnt[kMaxBins];   // pass 1: rows per bin
+    unsigned long long cursor[kMaxBins];    // pass 2: fill cursor per bin
+    unsigned long long bin_sum[kMaxBins];   // pass 1: sum of the sizes per bin
+    unsigned long long bin_nnza[kMaxBins];  // pass 1: A entries of the bin's rows
+    unsigned long long max_size;
+    unsigned long long total;
+};
+
+// Kernel table entry (host side).
+struct KernelDesc {
+    int tpr;          // threads per row (row group)
+    int block;        // threads per block
+    long long table;  // hash slots per row, or bitmap columns per pass
+    long long max_size;  // largest row size the kernel accepts
+    int bitmap;       // 1: shared-memory column bitmap kernel
+    size_t smem;      // dynamic shared memory per block
+};
+
+// --- setup.cu ----------------------------------------------------------------
+cudaError_t launch_nprod(const Operands &op, int64_t *nprod, int grid, cudaStream_t s);
+cudaError_t launch_bin_pass1(const int64_t *sizes, int64_t n, const Ranges &rg,
+                             const Operands &op, Counters *cnt, long long *tile_sums,
+                             cudaStream_t s);
+cudaError_t launch_bin_pass2(const int64_t *sizes, int64_t n, const Ranges &rg,
+                             const long long *offsets, Counters *cnt, int32_t *bins,
+                             cudaStream_t s);
+// In-place exclusive scan of crpt[0..n) using per-tile sums from pass 1;
+// writes crpt[n] = total. tile_sums needs room for ntiles + 1 entries.
+cudaError_t launch_scan(int64_t *crpt, int64_t n, long long *tile_sums, cudaStream_t s);
+int64_t bin_tile_rows();
+
+// --- symbolic.cu / numeric.cu -------------------------------------------------
+int sym_kernel_count();
+int num_kernel_count();
+const KernelDesc &sym_kernel(int id);
+const KernelDesc &num_kernel(int id);
+cudaError_t sym_prepare(int device_smem_optin);
+cudaError_t num_prepare(int device_smem_optin);
+cudaError_t launch_sym(int id, const Operands &op, const BinWork &w, size_t smem_bitmap,
+                       cudaStream_t s);
+cudaError_t launch_num(int id, const Operands &op, const BinWork &w, size_t smem_bitmap,
+                       cudaStream_t s);
+
+}  // namespace ops

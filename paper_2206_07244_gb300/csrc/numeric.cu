@@ -1,0 +1,347 @@
+// Numeric phase (Sec. 2.2, Sec. 5.2, Algorithm 5, Sec. 5.6.2): the sorted
+// column indices and summed values of each output row, written at the row
+// offsets that the scan left in C.rpt.
+//
+// Bins 0..8: a row group of TPR threads owns a shared-memory table of T
+// (int32 key, float64 value) slots, 12 bytes each, keys -1 = empty. Each
+// product probes with one atomicCAS; on an empty slot or the same key the
+// value is added with a shared-memory float64 atomicAdd (Algorithm 5). Then
+// the three phases of Sec. 5.6.2 follow: condense the occupied slots to the
+// front of the table (ballot/popc prefix per chunk of TPR slots, in place),
+// sort them by column (bitonic network in shared memory over the next power
+// of two), and store them with coalesced writes. The row size is known from
+// the symbolic phase and checked.
+//
+// Rows past the largest table go to num_bitmap_kernel (one 1024-thread block
+// per row). Pass 1 marks the row's columns in a shared-memory bitmap (set
+// with 32-bit atomicOr, read as 64-bit words) and forms per-word prefix counts, which give every column its rank
+// in the sorted row: C.col is written straight from the bitmap in column
+// order, no sort needed. Pass 2 adds each product into C.val[rank] with a
+// float64 atomicAdd in global memory (L2). 227 KB cover 1.2M columns per
+// pass; wider matrices take several column windows. This replaces the
+// paper's global-memory hash kernel (its kernel 7) and its condense/sort.
+#include <climits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace ops {
+
+template <int T>
+__device__ __forceinline__ void num_insert(int *tk, double *tv, int key, double v, int *err) {
+    uint32_t h = hash_slot<T>(key);
+    for (int it = 0; it < T; ++it) {
+        const int old = atomicCAS(tk + h, -1, key);
+        if (old == -1 || old == key) {
+            atomicAdd(tv + h, v);
+            return;
+        }
+        h = next_slot<T>(h);
+    }
+    set_error(err, DERR_TABLE_FULL);
+}
+
+// Mean referenced B-row length decides how many threads walk one B row; the
+// symbolic phase's n_prod is gone by now (C.rpt holds offsets), so the row
+// group recomputes it from B.rpt (those lines are needed right after).
+template <int TPR>
+__device__ __forceinline__ int numeric_lanes(const Operands &op, int fixed, int64_t p0,
+                                             int64_t p1, int lg, long long *red) {
+    if (fixed > 0) return pick_lanes(fixed, 0, 1, TPR);
+    long long sum = 0;
+    for (int64_t p = p0 + lg; p < p1; p += TPR) {
+        const int k = __ldg(op.acol + p);
+        sum += ld_rpt(op.brpt, op.b64, k + 1) - ld_rpt(op.brpt, op.b64, k);
+    }
+    sum = group_sum<TPR>(sum, red);
+    return pick_lanes(0, sum, p1 - p0, TPR);
+}
+
+// Minimum resident blocks: enough for 2048 threads per SM (<= 32 registers
+// per thread, Sec. 5.6) unless the table is so large that one block fills
+// the SM's shared memory anyway.
+template <int TPR, int BLOCK, int T>
+__global__ void __launch_bounds__(BLOCK, (T * 12 * (BLOCK / TPR) > 110 * 1024) ? 1 : 2048 / BLOCK)
+num_hash_kernel(Operands op, BinWork w) {
+    constexpr int RPB = BLOCK / TPR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *vals_all = reinterpret_cast<double *>(smem_raw);
+    int *keys_all = reinterpret_cast<int *>(vals_all + RPB * T);
+    __shared__ long long red64[32];
+    __shared__ int red32[33];
+    const int g = threadIdx.x / TPR, lg = threadIdx.x % TPR;
+    int *tk = keys_all + g * T;
+    double *tv = vals_all + g * T;
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * RPB + g;
+    const bool valid = r < w.cnt;
+    const int64_t row = valid ? (w.bins ? static_cast<int64_t>(w.bins[w.off + r]) : w.off + r) : 0;
+    for (int s = lg; s < T; s += TPR) {
+        tk[s] = -1;
+        tv[s] = 0.0;
+    }
+    int64_t cbase = 0, n_expect = 0, p0 = 0, p1 = 0;
+    if (valid) {
+        cbase = w.crpt[row];
+        n_expect = w.crpt[row + 1] - cbase;
+        const int64_t ar = op.row0 + row;
+        p0 = ld_rpt(op.arpt, op.a64, ar);
+        p1 = ld_rpt(op.arpt, op.a64, ar + 1);
+    }
+    const int S = numeric_lanes<TPR>(op, w.lanes, p0, p1, lg, red64);
+    group_sync<TPR>();
+    {
+        const int nsub = TPR / S, sub = lg / S, ls = lg % S;
+        for (int64_t p = p0 + sub; p < p1; p += nsub) {
+            const int k = __ldg(op.acol + p);
+            const double a = __ldg(op.aval + p);
+            const int64_t q1 = ld_rpt(op.brpt, op.b64, k + 1);
+            for (int64_t q = ld_rpt(op.brpt, op.b64, k) + ls; q < q1; q += S)
+                num_insert<T>(tk, tv, __ldg(op.bcol + q), a * __ldg(op.bval + q), w.err);
+        }
+    }
+    group_sync<TPR>();
+    // condense: occupied slots move to the front, chunk by chunk; a write
+    // never lands past the chunk that was just read.
+    int n = 0;
+    for (int c = 0; c < T; c += TPR) {
+        const int s = c + lg;
+        int k = -1;
+        double v = 0.0;
+        if (s < T) {
+            k = tk[s];
+            v = tv[s];
+        }
+        int pre, tot;
+        group_excl_count<TPR>(k >= 0, pre, tot, red32);
+        group_sync<TPR>();
+        if (k >= 0) {
+            tk[n + pre] = k;
+            tv[n + pre] = v;
+        }
+        n += tot;
+        group_sync<TPR>();
+    }
+    if (valid && n != n_expect) set_error(w.err, DERR_COUNT_MISMATCH);
+    int P = 1;
+    while (P < n) P <<= 1;
+    if (P > T) {  // cannot happen within the kernel's capacity; never index past the table
+        set_error(w.err, DERR_TABLE_FULL);
+        P = 1;
+    }
+    for (int s = n + lg; s < P; s += TPR) tk[s] = INT_MAX;
+    group_sync<TPR>();
+    // bitonic sort of (key, value) pairs over P entries, ascending
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lg; i < P; i += TPR) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const int ka = tk[i], kb = tk[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((ka > kb) == up) {
+                        tk[i] = kb;
+                        tk[ixj] = ka;
+                        const double va = tv[i];
+                        tv[i] = tv[ixj];
+                        tv[ixj] = va;
+                    }
+                }
+            }
+            group_sync<TPR>();
+        }
+    }
+    if (valid) {
+        const int64_t m = n < n_expect ? n : n_expect;
+        for (int64_t t = lg; t < m; t += TPR) {
+            w.ccol[cbase + t] = tk[t];
+            w.cval[cbase + t] = tv[t];
+        }
+    }
+}
+
+constexpr int kBmBlock = 1024;
+
+// Exclusive scan of one unsigned per thread over a 1024-thread block.
+__device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned &total, unsigned *sw) {
+    const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    unsigned inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= static_cast<unsigned>(o)) inc += y;
+    }
+    __syncthreads();
+    if (lane == 31) sw[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const unsigned t = sw[lane];
+        unsigned ti = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= static_cast<unsigned>(o)) ti += y;
+        }
+        sw[lane] = ti - t;
+        if (lane == 31) sw[32] = ti;
+    }
+    __syncthreads();
+    total = sw[32];
+    return sw[w] + inc - x;
+}
+
+__global__ void __launch_bounds__(kBmBlock, 1)
+num_bitmap_kernel(Operands op, BinWork w, int words) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long *bm = reinterpret_cast<unsigned long long *>(smem_raw);
+    unsigned *bm32 = reinterpret_cast<unsigned *>(smem_raw);   // same words, 32-bit halves
+    unsigned *pre = reinterpret_cast<unsigned *>(bm + words);
+    __shared__ long long red64[32];
+    __shared__ unsigned sw[33];
+    const int64_t row = w.bins ? static_cast<int64_t>(w.bins[w.off + blockIdx.x])
+                               : w.off + static_cast<int64_t>(blockIdx.x);
+    const int64_t cbase = w.crpt[row];
+    const int64_t n_expect = w.crpt[row + 1] - cbase;
+    const int64_t ar = op.row0 + row;
+    const int64_t p0 = ld_rpt(op.arpt, op.a64, ar);
+    const int64_t p1 = ld_rpt(op.arpt, op.a64, ar + 1);
+    const int S = numeric_lanes<kBmBlock>(op, w.lanes, p0, p1, threadIdx.x, red64);
+    const int nsub = kBmBlock / S, sub = threadIdx.x / S, ls = threadIdx.x % S;
+    const int64_t span = static_cast<int64_t>(words) * 64;
+    int64_t done = 0;
+    bool ok = true;
+    for (int64_t c0 = 0; c0 < op.ncols; c0 += span) {
+        const int nw = static_cast<int>(((op.ncols - c0 < span ? op.ncols - c0 : span) + 63) / 64);
+        for (int i = threadIdx.x; i < nw; i += kBmBlock) bm[i] = 0ull;
+        __syncthreads();
+        // pass 1: the row's columns inside this window
+        for (int64_t p = p0 + sub; p < p1; p += nsub) {
+            const int k = __ldg(op.acol + p);
+            const int64_t q1 = ld_rpt(op.brpt, op.b64, k + 1);
+            for (int64_t q = ld_rpt(op.brpt, op.b64, k) + ls; q < q1; q += S) {
+                const int64_t rel = static_cast<int64_t>(__ldg(op.bcol + q)) - c0;
+                // 32-bit atomics on the two halves of a 64-bit word: shared
+                // 64-bit atomics run several times slower on this GPU
+                if (rel >= 0 && rel < span) atomicOr(bm32 + (rel >> 5), 1u << (rel & 31));
+            }
+        }
+        __syncthreads();
+        // per-word prefix counts = rank of a word's first column in the window
+        unsigned run = 0;
+        for (int b = 0; b < nw; b += kBmBlock) {
+            const int i = b + static_cast<int>(threadIdx.x);
+            const unsigned c = i < nw ? static_cast<unsigned>(__popcll(bm[i])) : 0u;
+            unsigned tot;
+            const unsigned ex = block_excl_scan(c, tot, sw);
+            if (i < nw) pre[i] = run + ex;
+            run += tot;
+        }
+        __syncthreads();
+        const int64_t cnt = run;
+        if (done + cnt > n_expect) ok = false;   // uniform: cnt and done are block-wide
+        if (ok) {
+            int32_t *ccol = w.ccol + cbase + done;
+            double *cval = w.cval + cbase + done;
+            for (int i = threadIdx.x; i < nw; i += kBmBlock) {
+                unsigned long long x = bm[i];
+                unsigned pos = pre[i];
+                const int colbase = static_cast<int>(c0) + i * 64;
+                while (x) {
+                    const int b = __ffsll(static_cast<long long>(x)) - 1;
+                    x &= x - 1;
+                    ccol[pos++] = colbase + b;
+                }
+            }
+            for (int64_t t = threadIdx.x; t < cnt; t += kBmBlock) cval[t] = 0.0;
+            __syncthreads();
+            // pass 2: each product lands on its column's rank
+            for (int64_t p = p0 + sub; p < p1; p += nsub) {
+                const int k = __ldg(op.acol + p);
+                const double a = __ldg(op.aval + p);
+                const int64_t q1 = ld_rpt(op.brpt, op.b64, k + 1);
+                for (int64_t q = ld_rpt(op.brpt, op.b64, k) + ls; q < q1; q += S) {
+                    const int64_t rel = static_cast<int64_t>(__ldg(op.bcol + q)) - c0;
+                    if (rel >= 0 && rel < span) {
+                        const int wi = static_cast<int>(rel >> 6);
+                        const int bi = static_cast<int>(rel & 63);
+                        const unsigned rank = pre[wi] +
+                            static_cast<unsigned>(__popcll(bm[wi] & ((1ull << bi) - 1ull)));
+                        atomicAdd(cval + rank, a * __ldg(op.bval + q));
+                    }
+                }
+            }
+        }
+        done += cnt;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && (!ok || done != n_expect)) set_error(w.err, DERR_COUNT_MISMATCH);
+}
+
+// --- kernel table ---------------------------------------------------------------
+using NumFn = void (*)(Operands, BinWork);
+
+#define NUM_TABLE(X)                 \
+    X(8, 256, 32)                    \
+    X(16, 256, 128)                  \
+    X(32, 256, 256)                  \
+    X(64, 64, 512)                   \
+    X(128, 128, 1024)                \
+    X(256, 256, 2048)                \
+    X(512, 512, 4096)                \
+    X(1024, 1024, 8192)              \
+    X(1024, 1024, 18432)
+
+struct NumEntry {
+    KernelDesc d;
+    NumFn fn;
+};
+
+// Largest row the table can sort in place: the bitonic network needs the
+// next power of two of the row size to fit in the table.
+constexpr long long pow2_floor(long long t) {
+    long long p = 1;
+    while (p * 2 <= t) p *= 2;
+    return p;
+}
+
+#define NUM_ENTRY(TPR, BLOCK, T)                                                        \
+    {{TPR, BLOCK, T, pow2_floor(T), 0, (sizeof(int) + sizeof(double)) * (BLOCK / TPR) * (size_t)T}, \
+     &num_hash_kernel<TPR, BLOCK, T>},
+
+static NumEntry g_num[] = {NUM_TABLE(NUM_ENTRY)};
+static constexpr int kNumHash = sizeof(g_num) / sizeof(g_num[0]);
+static KernelDesc g_num_bitmap{kBmBlock, kBmBlock, 0, LLONG_MAX, 1, 0};
+
+int num_kernel_count() { return kNumHash + 1; }
+
+const KernelDesc &num_kernel(int id) {
+    return id < kNumHash ? g_num[id].d : g_num_bitmap;
+}
+
+cudaError_t num_prepare(int smem_optin) {
+    // Opt in for every kernel: the 48 KB default covers static plus dynamic
+    // shared memory, so a table of exactly 48 KB already needs it.
+    for (int i = 0; i < kNumHash; ++i) {
+        cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(g_num[i].fn),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(g_num[i].d.smem));
+        if (e != cudaSuccess) return e;
+    }
+    g_num_bitmap.table = static_cast<long long>(smem_optin / 12) * 64;
+    return cudaFuncSetAttribute(reinterpret_cast<const void *>(&num_bitmap_kernel),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+}
+
+cudaError_t launch_num(int id, const Operands &op, const BinWork &w, size_t smem_bitmap,
+                       cudaStream_t s) {
+    if (w.cnt <= 0) return cudaSuccess;
+    if (id < kNumHash) {
+        const KernelDesc &d = g_num[id].d;
+        const int rpb = d.block / d.tpr;
+        const int64_t grid = (w.cnt + rpb - 1) / rpb;
+        g_num[id].fn<<<static_cast<unsigned>(grid), d.block, d.smem, s>>>(op, w);
+    } else {
+        const int words = static_cast<int>(smem_bitmap / 12);
+        num_bitmap_kernel<<<static_cast<unsigned>(w.cnt), kBmBlock, smem_bitmap, s>>>(op, w, words);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ops

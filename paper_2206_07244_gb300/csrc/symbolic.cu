@@ -1,0 +1,175 @@
+// Symbolic phase (Sec. 2.2, Sec. 5.2, Algorithm 4): the number of distinct
+// column keys of each output row, written over n_prod in C.rpt.
+//
+// Bins 0..8 use shared-memory hash tables. A row group of TPR threads owns one
+// table of T int32 slots (-1 = empty). Each probe is one atomicCAS whose
+// returned value decides everything (the paper's single-access probe, Sec.
+// 5.2): -1 means the key was new, the key itself means it was already there,
+// anything else moves to the next slot. Every probe loop is bounded by the
+// table size, so a full table raises an error flag instead of spinning.
+// New keys are counted in a register per thread and summed once per row
+// instead of one shared atomicAdd per new key.
+//
+// Table sizes are chosen for GB300's 228 KB of shared memory and 2048 threads
+// per SM: kernels 0-7 keep full occupancy (their table bytes per thread fit
+// 228 KB / 2048), kernel 8 trades occupancy for a 128 KB table (the role of
+// the paper's kernel 7).
+//
+// Rows past the largest table go to sym_bitmap_kernel: one 1024-thread block
+// per row keeps a bitmap of the column space in shared memory (227 KB hold
+// 1.86M columns; wider matrices are covered in several passes over column
+// windows), sets one bit per product with atomicOr and counts bits with
+// popc. It replaces the paper's kernel 7 -> kernel 8 global-hash recompute:
+// no key ever leaves shared memory and nothing has to be recomputed.
+#include <climits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace ops {
+
+template <int T>
+__device__ __forceinline__ int sym_insert(int *tab, int key, int *err) {
+    uint32_t h = hash_slot<T>(key);
+    for (int it = 0; it < T; ++it) {
+        const int old = atomicCAS(tab + h, -1, key);
+        if (old == -1) return 1;
+        if (old == key) return 0;
+        h = next_slot<T>(h);
+    }
+    set_error(err, DERR_TABLE_FULL);
+    return 0;
+}
+
+// Minimum resident blocks: enough for 2048 threads per SM (<= 32 registers
+// per thread, Sec. 5.6) unless the table is so large that one block fills
+// the SM's shared memory anyway.
+template <int TPR, int BLOCK, int T>
+__global__ void __launch_bounds__(BLOCK, (T * 4 * (BLOCK / TPR) > 110 * 1024) ? 1 : 2048 / BLOCK)
+sym_hash_kernel(Operands op, BinWork w) {
+    constexpr int RPB = BLOCK / TPR;
+    extern __shared__ int smem_tab[];
+    __shared__ long long red[32];
+    const int g = threadIdx.x / TPR, lg = threadIdx.x % TPR;
+    int *tab = smem_tab + g * T;
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * RPB + g;
+    const bool valid = r < w.cnt;
+    const int64_t row = valid ? (w.bins ? static_cast<int64_t>(w.bins[w.off + r]) : w.off + r) : 0;
+    for (int s = lg; s < T; s += TPR) tab[s] = -1;
+    group_sync<TPR>();
+    long long cnt = 0;
+    if (valid) {
+        const int64_t ar = op.row0 + row;
+        const int64_t p0 = ld_rpt(op.arpt, op.a64, ar);
+        const int64_t p1 = ld_rpt(op.arpt, op.a64, ar + 1);
+        const int S = pick_lanes(w.lanes, w.crpt[row], p1 - p0, TPR);
+        const int nsub = TPR / S, sub = lg / S, ls = lg % S;
+        for (int64_t p = p0 + sub; p < p1; p += nsub) {
+            const int k = __ldg(op.acol + p);
+            const int64_t q1 = ld_rpt(op.brpt, op.b64, k + 1);
+            for (int64_t q = ld_rpt(op.brpt, op.b64, k) + ls; q < q1; q += S)
+                cnt += sym_insert<T>(tab, __ldg(op.bcol + q), w.err);
+        }
+    }
+    cnt = group_sum<TPR>(cnt, red);
+    if (valid && lg == 0) w.crpt[row] = cnt;
+}
+
+constexpr int kBmBlock = 1024;
+
+__global__ void __launch_bounds__(kBmBlock, 1)
+sym_bitmap_kernel(Operands op, BinWork w, int words) {
+    extern __shared__ unsigned bm[];
+    __shared__ long long red[32];
+    const int64_t row = w.bins ? static_cast<int64_t>(w.bins[w.off + blockIdx.x])
+                               : w.off + static_cast<int64_t>(blockIdx.x);
+    const int64_t ar = op.row0 + row;
+    const int64_t p0 = ld_rpt(op.arpt, op.a64, ar);
+    const int64_t p1 = ld_rpt(op.arpt, op.a64, ar + 1);
+    const int S = pick_lanes(w.lanes, w.crpt[row], p1 - p0, 32);
+    const int nsub = kBmBlock / S, sub = threadIdx.x / S, ls = threadIdx.x % S;
+    const int64_t span = static_cast<int64_t>(words) * 32;
+    long long total = 0;
+    for (int64_t c0 = 0; c0 < op.ncols; c0 += span) {
+        const int nw = static_cast<int>(((op.ncols - c0 < span ? op.ncols - c0 : span) + 31) / 32);
+        for (int i = threadIdx.x; i < nw; i += kBmBlock) bm[i] = 0u;
+        __syncthreads();
+        for (int64_t p = p0 + sub; p < p1; p += nsub) {
+            const int k = __ldg(op.acol + p);
+            const int64_t q1 = ld_rpt(op.brpt, op.b64, k + 1);
+            for (int64_t q = ld_rpt(op.brpt, op.b64, k) + ls; q < q1; q += S) {
+                const int64_t rel = static_cast<int64_t>(__ldg(op.bcol + q)) - c0;
+                if (rel >= 0 && rel < span)
+                    atomicOr(bm + (rel >> 5), 1u << (rel & 31));
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nw; i += kBmBlock) total += __popc(bm[i]);
+        __syncthreads();
+    }
+    total = group_sum<kBmBlock>(total, red);
+    if (threadIdx.x == 0) w.crpt[row] = total;
+}
+
+// --- kernel table ---------------------------------------------------------------
+using SymFn = void (*)(Operands, BinWork);
+
+#define SYM_TABLE(X)                 \
+    X(8, 256, 64)                    \
+    X(16, 256, 256)                  \
+    X(32, 256, 512)                  \
+    X(64, 64, 1024)                  \
+    X(128, 128, 2048)                \
+    X(256, 256, 4096)                \
+    X(512, 512, 8192)                \
+    X(1024, 1024, 16384)             \
+    X(1024, 1024, 32768)
+
+struct SymEntry {
+    KernelDesc d;
+    SymFn fn;
+};
+
+#define SYM_ENTRY(TPR, BLOCK, T) \
+    {{TPR, BLOCK, T, T, 0, sizeof(int) * (BLOCK / TPR) * (size_t)T}, &sym_hash_kernel<TPR, BLOCK, T>},
+
+static SymEntry g_sym[] = {SYM_TABLE(SYM_ENTRY)};
+static constexpr int kSymHash = sizeof(g_sym) / sizeof(g_sym[0]);
+static KernelDesc g_sym_bitmap{kBmBlock, kBmBlock, 0, LLONG_MAX, 1, 0};
+
+int sym_kernel_count() { return kSymHash + 1; }
+
+const KernelDesc &sym_kernel(int id) {
+    return id < kSymHash ? g_sym[id].d : g_sym_bitmap;
+}
+
+cudaError_t sym_prepare(int smem_optin) {
+    // Opt in for every kernel: the 48 KB default covers static plus dynamic
+    // shared memory, so a table of exactly 48 KB already needs it.
+    for (int i = 0; i < kSymHash; ++i) {
+        cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(g_sym[i].fn),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(g_sym[i].d.smem));
+        if (e != cudaSuccess) return e;
+    }
+    g_sym_bitmap.table = static_cast<long long>(smem_optin / 4) * 32;
+    return cudaFuncSetAttribute(reinterpret_cast<const void *>(&sym_bitmap_kernel),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+}
+
+cudaError_t launch_sym(int id, const Operands &op, const BinWork &w, size_t smem_bitmap,
+                       cudaStream_t s) {
+    if (w.cnt <= 0) return cudaSuccess;
+    if (id < kSymHash) {
+        const KernelDesc &d = g_sym[id].d;
+        const int rpb = d.block / d.tpr;
+        const int64_t grid = (w.cnt + rpb - 1) / rpb;
+        g_sym[id].fn<<<static_cast<unsigned>(grid), d.block, d.smem, s>>>(op, w);
+    } else {
+        const int words = static_cast<int>(smem_bitmap / 4);
+        sym_bitmap_kernel<<<static_cast<unsigned>(w.cnt), kBmBlock, smem_bitmap, s>>>(op, w, words);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ops
