@@ -201,6 +201,7 @@ int spgemm_kernel_info(int phase, int id, int32_t *threads_per_row,
 
 const char *spgemm_strerror(int code);
 
+
 #ifdef __cplusplus
 }
 #endif

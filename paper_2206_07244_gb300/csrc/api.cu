@@ -20,6 +20,7 @@
 #include <cstring>
 #include <new>
 
+#include "common.cuh"
 #include "internal.h"
 #include "opsparse.h"
 
@@ -77,6 +78,7 @@ struct spgemm_handle {
     int64_t *stage_rpt = nullptr;
     size_t stage_rpt_n = 0;
     bool timing = false;
+    bool serial = false;   // timing mode 2: every bin kernel on the main stream, one after another
     cudaEvent_t t0[kSlots] = {}, t1[kSlots] = {};
     bool pending[kSlots] = {};
     double ms[kSlots] = {};
@@ -254,8 +256,8 @@ int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *s
     int used = 0;
     for (int j = nb - 1; j >= 0; --j) {
         if (size[j] <= 0) continue;
-        cudaStream_t s = h->side[used % kSide];
-        if (used < kSide) CK(cudaStreamWaitEvent(s, h->ev_fork, 0));
+        cudaStream_t s = h->serial ? h->stream : h->side[used % kSide];
+        if (!h->serial && used < kSide) CK(cudaStreamWaitEvent(s, h->ev_fork, 0));
         BinWork w;
         w.bins = identity ? nullptr : d_bins(h);
         w.off = identity ? 0 : offset[j];
@@ -266,11 +268,13 @@ int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *s
         const KernelDesc &d = phase ? num_kernel(kid[j]) : sym_kernel(kid[j]);
         size_t smem = 0;
         if (d.bitmap) {
+            // bitmap bytes; the kernels add their walk scratch on top
+            const int64_t budget = h->smem_dyn_max - static_cast<int64_t>(sizeof(WalkScratch));
             if (phase == 0) {
-                const int64_t words = std::min<int64_t>((op.ncols + 31) / 32, h->smem_dyn_max / 4);
+                const int64_t words = std::min<int64_t>((op.ncols + 31) / 32, budget / 4);
                 smem = static_cast<size_t>(std::max<int64_t>(words, 1)) * 4;
             } else {
-                const int64_t words = std::min<int64_t>((op.ncols + 63) / 64, h->smem_dyn_max / 12);
+                const int64_t words = std::min<int64_t>((op.ncols + 63) / 64, budget / 12);
                 smem = static_cast<size_t>(std::max<int64_t>(words, 1)) * 12;
             }
         }
@@ -280,7 +284,7 @@ int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *s
         time_end(h, slot, s);
         ++used;
     }
-    for (int i = 0; i < std::min(used, kSide); ++i) {
+    for (int i = 0; !h->serial && i < std::min(used, kSide); ++i) {
         CK(cudaEventRecord(h->ev_side[i], h->side[i]));
         CK(cudaStreamWaitEvent(h->stream, h->ev_side[i], 0));
     }
@@ -694,19 +698,47 @@ int spgemm_multiply_host(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_
             release_all();
             return SPGEMM_ERR_CUDA;
         }
+    // Each chunk's copy is split into kCopyParts pieces on the side streams,
+    // so several copy engines move it at once.
+    constexpr int kCopyParts = 4;
+    cudaEvent_t part_done[2][kCopyParts] = {};
+    for (auto &row : part_done)
+        for (auto &e : row)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                release_all();
+                return SPGEMM_ERR_CUDA;
+            }
+    if (cudaEventRecord(h->ev_fork, h->stream) != cudaSuccess) {
+        release_all();
+        return SPGEMM_ERR_CUDA;
+    }
+    for (int k = 0; k < kCopyParts; ++k) cudaStreamWaitEvent(h->side[k], h->ev_fork, 0);
     auto enqueue = [&](const Chunk &c, int b) -> bool {
         const int64_t n = rpt[c.r1] - rpt[c.r0];
         if (12 * n > chunk_bytes) return false;  // one row larger than a chunk
         unsigned char *buf = h->stage + (size_t)b * (size_t)chunk_bytes;
-        if (n) {
-            if (cudaMemcpyAsync(buf, C.col + rpt[c.r0], sizeof(int32_t) * (size_t)n,
-                                cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
-                cudaMemcpyAsync(buf + ((sizeof(int32_t) * (size_t)n + 255) & ~size_t(255)),
-                                C.val + rpt[c.r0], sizeof(double) * (size_t)n,
-                                cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
-                return false;
+        int32_t *hcol = reinterpret_cast<int32_t *>(buf);
+        double *hval = reinterpret_cast<double *>(buf + ((sizeof(int32_t) * (size_t)n + 255) & ~size_t(255)));
+        // the host may still be reading buffer b from two chunks ago: the
+        // sink for it returned before this enqueue, so it is free now
+        for (int k = 0; k < kCopyParts; ++k) {
+            const int64_t lo = n * k / kCopyParts, hi = n * (k + 1) / kCopyParts;
+            cudaStream_t s = h->side[k];
+            if (hi > lo) {
+                if (cudaMemcpyAsync(hcol + lo, C.col + rpt[c.r0] + lo, sizeof(int32_t) * (size_t)(hi - lo),
+                                    cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaMemcpyAsync(hval + lo, C.val + rpt[c.r0] + lo, sizeof(double) * (size_t)(hi - lo),
+                                    cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                    return false;
+            }
+            if (cudaEventRecord(part_done[b][k], s) != cudaSuccess) return false;
         }
-        return cudaEventRecord(done[b], h->stream) == cudaSuccess;
+        return true;
+    };
+    auto wait_chunk = [&](int b) -> bool {
+        for (int k = 0; k < kCopyParts; ++k)
+            if (cudaEventSynchronize(part_done[b][k]) != cudaSuccess) return false;
+        return true;
     };
     rc = SPGEMM_OK;
     if (C.rows > 0) {
@@ -720,7 +752,7 @@ int spgemm_multiply_host(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_
                 nxt = next_chunk(cur.r1);
                 if (!enqueue(nxt, b ^ 1)) { rc = SPGEMM_ERR_INVALID; break; }
             }
-            if (cudaEventSynchronize(done[b]) != cudaSuccess) { rc = SPGEMM_ERR_CUDA; break; }
+            if (!wait_chunk(b)) { rc = SPGEMM_ERR_CUDA; break; }
             const int64_t n = rpt[cur.r1] - rpt[cur.r0];
             unsigned char *buf = h->stage + (size_t)b * (size_t)chunk_bytes;
             const int32_t *hc = reinterpret_cast<const int32_t *>(buf);
@@ -735,8 +767,11 @@ int spgemm_multiply_host(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_
             b ^= 1;
         }
     }
+    for (int k = 0; k < kCopyParts; ++k) cudaStreamSynchronize(h->side[k]);
     cudaStreamSynchronize(h->stream);
     for (auto &e : done) cudaEventDestroy(e);
+    for (auto &row : part_done)
+        for (auto &e : row) cudaEventDestroy(e);
     release_all();
     if (rc == SPGEMM_OK && nnzC) *nnzC = nnz;
     return rc;
@@ -758,6 +793,7 @@ int spgemm_set_timing(spgemm_handle *h, int enable) {
         }
     }
     h->timing = enable != 0;
+    h->serial = enable == 2;
     return SPGEMM_OK;
 }
 

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "internal.h"
+
 namespace ops {
 
 // Device error codes written to the handle's error word (first one wins).
@@ -147,6 +149,110 @@ __device__ __forceinline__ int64_t upper_bound_rpt(const void *rpt, int is64, in
         if (ld_rpt(rpt, is64, mid) <= p) lo = mid; else hi = mid;
     }
     return lo;
+}
+
+}  // namespace ops
+
+namespace ops {
+
+// --- block-level walk over the products of one output row -------------------
+// A row's products are the entries of the B rows its A entries reference.
+// Giving each A entry to one sub-group leaves most of a block idle when a row
+// has few A entries with long B rows (common in power-law graphs). Instead,
+// A entries are read CH at a time, every referenced B row is cut into pieces
+// of at most W = S * kPieceIters products, and the block's sub-groups of S
+// lanes take pieces round-robin; a sub-group's lanes read a piece with unit
+// stride (coalesced). The piece -> A entry map is a binary search over the
+// chunk's piece offsets in shared memory, paid once per piece.
+constexpr int kPieceIters = 4;
+constexpr int kWalkChunk = 256;
+
+struct WalkScratch {
+    long long q0[kWalkChunk];     // first B entry of each A entry's B row
+    double a[kWalkChunk];         // A value
+    int len[kWalkChunk];          // B row length
+    long long pstart[kWalkChunk + 1];  // exclusive piece offsets
+    long long warp_tot[33];
+};
+
+// Exclusive scan of one long long per thread over a block of BLOCK threads
+// (BLOCK a multiple of 32); returns the thread's prefix, `total` the sum.
+template <int BLOCK>
+__device__ __forceinline__ long long block_excl_scan_ll(long long x, long long &total,
+                                                        long long *sw) {
+    const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    long long inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= static_cast<unsigned>(o)) inc += y;
+    }
+    if constexpr (BLOCK == 32) {
+        total = __shfl_sync(0xffffffffu, inc, 31);
+        return inc - x;
+    } else {
+        __syncthreads();
+        if (lane == 31) sw[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            const long long t = lane < (BLOCK >> 5) ? sw[lane] : 0;
+            long long ti = t;
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, ti, o);
+                if (lane >= static_cast<unsigned>(o)) ti += y;
+            }
+            if (lane < (BLOCK >> 5)) sw[lane] = ti - t;
+            if (lane == 31) sw[32] = ti;
+        }
+        __syncthreads();
+        total = sw[32];
+        return sw[w] + inc - x;
+    }
+}
+
+// Calls f(key, a_value, q) for every product of the row [p0, p1) of A.
+// Every thread of the block must call it (it synchronises the block).
+template <int BLOCK, bool NEED_A, typename F>
+__device__ __forceinline__ void block_row_walk(const Operands &op, int64_t p0, int64_t p1, int S,
+                                               WalkScratch *sc, F &&f) {
+    static_assert(BLOCK >= 32 && BLOCK % 32 == 0, "block walk needs whole warps");
+    constexpr int CH = BLOCK < kWalkChunk ? BLOCK : kWalkChunk;
+    const int nsub = BLOCK / S, sub = threadIdx.x / S, ls = threadIdx.x % S;
+    const long long W = static_cast<long long>(S) * kPieceIters;
+    for (int64_t c = p0; c < p1; c += CH) {
+        const int cnt = static_cast<int>(p1 - c < CH ? p1 - c : CH);
+        long long pieces = 0;
+        if (threadIdx.x < CH) {
+            const int t = threadIdx.x;
+            if (t < cnt) {
+                const int k = __ldg(op.acol + c + t);
+                const long long q0 = ld_rpt(op.brpt, op.b64, k);
+                const long long len = ld_rpt(op.brpt, op.b64, k + 1) - q0;
+                sc->q0[t] = q0;
+                sc->len[t] = static_cast<int>(len);
+                if (NEED_A) sc->a[t] = __ldg(op.aval + c + t);
+                pieces = (len + W - 1) / W;
+            }
+        }
+        long long total;
+        const long long ex = block_excl_scan_ll<BLOCK>(pieces, total, sc->warp_tot);
+        if (threadIdx.x < CH) sc->pstart[threadIdx.x] = ex;
+        if (threadIdx.x == 0) sc->pstart[CH] = total;
+        __syncthreads();
+        for (long long it = sub; it < total; it += nsub) {
+            int lo = 0, hi = cnt;  // last e with pstart[e] <= it
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (sc->pstart[mid] <= it) lo = mid; else hi = mid;
+            }
+            const long long piece = it - sc->pstart[lo];
+            const long long qb = sc->q0[lo] + piece * W;
+            const long long qe0 = sc->q0[lo] + sc->len[lo];
+            const long long qe = qb + W < qe0 ? qb + W : qe0;
+            const double a = NEED_A ? sc->a[lo] : 0.0;
+            for (long long q = qb + ls; q < qe; q += S) f(__ldg(op.bcol + q), a, q);
+        }
+        __syncthreads();
+    }
 }
 
 }  // namespace ops

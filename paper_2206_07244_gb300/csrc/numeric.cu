@@ -89,7 +89,14 @@ num_hash_kernel(Operands op, BinWork w) {
     }
     const int S = numeric_lanes<TPR>(op, w.lanes, p0, p1, lg, red64);
     group_sync<TPR>();
-    {
+    if constexpr (TPR > 32) {
+        // one row per block: flattened walk over B-row pieces
+        WalkScratch *sc = reinterpret_cast<WalkScratch *>(
+            smem_raw + (sizeof(int) + sizeof(double)) * (size_t)RPB * T);
+        block_row_walk<BLOCK, true>(op, p0, p1, S, sc, [&](int key, double a, long long q) {
+            num_insert<T>(tk, tv, key, a * __ldg(op.bval + q), w.err);
+        });
+    } else {
         const int nsub = TPR / S, sub = lg / S, ls = lg % S;
         for (int64_t p = p0 + sub; p < p1; p += nsub) {
             const int k = __ldg(op.acol + p);
@@ -190,8 +197,9 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned &total,
 __global__ void __launch_bounds__(kBmBlock, 1)
 num_bitmap_kernel(Operands op, BinWork w, int words) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned long long *bm = reinterpret_cast<unsigned long long *>(smem_raw);
-    unsigned *bm32 = reinterpret_cast<unsigned *>(smem_raw);   // same words, 32-bit halves
+    WalkScratch *sc = reinterpret_cast<WalkScratch *>(smem_raw);
+    unsigned long long *bm = reinterpret_cast<unsigned long long *>(smem_raw + sizeof(WalkScratch));
+    unsigned *bm32 = reinterpret_cast<unsigned *>(bm);   // same words, 32-bit halves
     unsigned *pre = reinterpret_cast<unsigned *>(bm + words);
     __shared__ long long red64[32];
     __shared__ unsigned sw[33];
@@ -203,7 +211,6 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
     const int64_t p0 = ld_rpt(op.arpt, op.a64, ar);
     const int64_t p1 = ld_rpt(op.arpt, op.a64, ar + 1);
     const int S = numeric_lanes<kBmBlock>(op, w.lanes, p0, p1, threadIdx.x, red64);
-    const int nsub = kBmBlock / S, sub = threadIdx.x / S, ls = threadIdx.x % S;
     const int64_t span = static_cast<int64_t>(words) * 64;
     int64_t done = 0;
     bool ok = true;
@@ -211,18 +218,13 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
         const int nw = static_cast<int>(((op.ncols - c0 < span ? op.ncols - c0 : span) + 63) / 64);
         for (int i = threadIdx.x; i < nw; i += kBmBlock) bm[i] = 0ull;
         __syncthreads();
-        // pass 1: the row's columns inside this window
-        for (int64_t p = p0 + sub; p < p1; p += nsub) {
-            const int k = __ldg(op.acol + p);
-            const int64_t q1 = ld_rpt(op.brpt, op.b64, k + 1);
-            for (int64_t q = ld_rpt(op.brpt, op.b64, k) + ls; q < q1; q += S) {
-                const int64_t rel = static_cast<int64_t>(__ldg(op.bcol + q)) - c0;
-                // 32-bit atomics on the two halves of a 64-bit word: shared
-                // 64-bit atomics run several times slower on this GPU
-                if (rel >= 0 && rel < span) atomicOr(bm32 + (rel >> 5), 1u << (rel & 31));
-            }
-        }
-        __syncthreads();
+        // pass 1: the row's columns inside this window. 32-bit atomics on the
+        // two halves of a 64-bit word: shared 64-bit atomics run several
+        // times slower on this GPU
+        block_row_walk<kBmBlock, false>(op, p0, p1, S, sc, [&](int key, double, long long) {
+            const int64_t rel = static_cast<int64_t>(key) - c0;
+            if (rel >= 0 && rel < span) atomicOr(bm32 + (rel >> 5), 1u << (rel & 31));
+        });
         // per-word prefix counts = rank of a word's first column in the window
         unsigned run = 0;
         for (int b = 0; b < nw; b += kBmBlock) {
@@ -252,21 +254,16 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
             for (int64_t t = threadIdx.x; t < cnt; t += kBmBlock) cval[t] = 0.0;
             __syncthreads();
             // pass 2: each product lands on its column's rank
-            for (int64_t p = p0 + sub; p < p1; p += nsub) {
-                const int k = __ldg(op.acol + p);
-                const double a = __ldg(op.aval + p);
-                const int64_t q1 = ld_rpt(op.brpt, op.b64, k + 1);
-                for (int64_t q = ld_rpt(op.brpt, op.b64, k) + ls; q < q1; q += S) {
-                    const int64_t rel = static_cast<int64_t>(__ldg(op.bcol + q)) - c0;
-                    if (rel >= 0 && rel < span) {
-                        const int wi = static_cast<int>(rel >> 6);
-                        const int bi = static_cast<int>(rel & 63);
-                        const unsigned rank = pre[wi] +
-                            static_cast<unsigned>(__popcll(bm[wi] & ((1ull << bi) - 1ull)));
-                        atomicAdd(cval + rank, a * __ldg(op.bval + q));
-                    }
+            block_row_walk<kBmBlock, true>(op, p0, p1, S, sc, [&](int key, double a, long long q) {
+                const int64_t rel = static_cast<int64_t>(key) - c0;
+                if (rel >= 0 && rel < span) {
+                    const int wi = static_cast<int>(rel >> 6);
+                    const int bi = static_cast<int>(rel & 63);
+                    const unsigned rank = pre[wi] +
+                        static_cast<unsigned>(__popcll(bm[wi] & ((1ull << bi) - 1ull)));
+                    atomicAdd(cval + rank, a * __ldg(op.bval + q));
                 }
-            }
+            });
         }
         done += cnt;
         __syncthreads();
@@ -301,8 +298,10 @@ constexpr long long pow2_floor(long long t) {
     return p;
 }
 
-#define NUM_ENTRY(TPR, BLOCK, T)                                                        \
-    {{TPR, BLOCK, T, pow2_floor(T), 0, (sizeof(int) + sizeof(double)) * (BLOCK / TPR) * (size_t)T}, \
+#define NUM_ENTRY(TPR, BLOCK, T)                                                         \
+    {{TPR, BLOCK, T, pow2_floor(T), 0,                                                   \
+      (sizeof(int) + sizeof(double)) * (BLOCK / TPR) * (size_t)T +                       \
+          (TPR > 32 ? sizeof(WalkScratch) : 0)},                                         \
      &num_hash_kernel<TPR, BLOCK, T>},
 
 static NumEntry g_num[] = {NUM_TABLE(NUM_ENTRY)};
@@ -324,7 +323,7 @@ cudaError_t num_prepare(int smem_optin) {
                                              static_cast<int>(g_num[i].d.smem));
         if (e != cudaSuccess) return e;
     }
-    g_num_bitmap.table = static_cast<long long>(smem_optin / 12) * 64;
+    g_num_bitmap.table = static_cast<long long>((smem_optin - sizeof(WalkScratch)) / 12) * 64;
     return cudaFuncSetAttribute(reinterpret_cast<const void *>(&num_bitmap_kernel),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
 }
@@ -339,7 +338,8 @@ cudaError_t launch_num(int id, const Operands &op, const BinWork &w, size_t smem
         g_num[id].fn<<<static_cast<unsigned>(grid), d.block, d.smem, s>>>(op, w);
     } else {
         const int words = static_cast<int>(smem_bitmap / 12);
-        num_bitmap_kernel<<<static_cast<unsigned>(w.cnt), kBmBlock, smem_bitmap, s>>>(op, w, words);
+        num_bitmap_kernel<<<static_cast<unsigned>(w.cnt), kBmBlock, smem_bitmap + sizeof(WalkScratch), s>>>(
+            op, w, words);
     }
     return cudaGetLastError();
 }

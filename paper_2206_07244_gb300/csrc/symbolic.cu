@@ -48,7 +48,8 @@ template <int TPR, int BLOCK, int T>
 __global__ void __launch_bounds__(BLOCK, (T * 4 * (BLOCK / TPR) > 110 * 1024) ? 1 : 2048 / BLOCK)
 sym_hash_kernel(Operands op, BinWork w) {
     constexpr int RPB = BLOCK / TPR;
-    extern __shared__ int smem_tab[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int *smem_tab = reinterpret_cast<int *>(smem_raw);
     __shared__ long long red[32];
     const int g = threadIdx.x / TPR, lg = threadIdx.x % TPR;
     int *tab = smem_tab + g * T;
@@ -58,7 +59,17 @@ sym_hash_kernel(Operands op, BinWork w) {
     for (int s = lg; s < T; s += TPR) tab[s] = -1;
     group_sync<TPR>();
     long long cnt = 0;
-    if (valid) {
+    if constexpr (TPR > 32) {
+        // one row per block (grid = rows): flattened walk over B-row pieces
+        WalkScratch *sc = reinterpret_cast<WalkScratch *>(smem_raw + sizeof(int) * (size_t)T);
+        const int64_t ar = op.row0 + row;
+        const int64_t p0 = ld_rpt(op.arpt, op.a64, ar);
+        const int64_t p1 = ld_rpt(op.arpt, op.a64, ar + 1);
+        const int S = pick_lanes(w.lanes, w.crpt[row], p1 - p0, 32);
+        block_row_walk<BLOCK, false>(op, p0, p1, S, sc, [&](int key, double, long long) {
+            cnt += sym_insert<T>(tab, key, w.err);
+        });
+    } else if (valid) {
         const int64_t ar = op.row0 + row;
         const int64_t p0 = ld_rpt(op.arpt, op.a64, ar);
         const int64_t p1 = ld_rpt(op.arpt, op.a64, ar + 1);
@@ -79,7 +90,9 @@ constexpr int kBmBlock = 1024;
 
 __global__ void __launch_bounds__(kBmBlock, 1)
 sym_bitmap_kernel(Operands op, BinWork w, int words) {
-    extern __shared__ unsigned bm[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WalkScratch *sc = reinterpret_cast<WalkScratch *>(smem_raw);
+    unsigned *bm = reinterpret_cast<unsigned *>(smem_raw + sizeof(WalkScratch));
     __shared__ long long red[32];
     const int64_t row = w.bins ? static_cast<int64_t>(w.bins[w.off + blockIdx.x])
                                : w.off + static_cast<int64_t>(blockIdx.x);
@@ -87,23 +100,16 @@ sym_bitmap_kernel(Operands op, BinWork w, int words) {
     const int64_t p0 = ld_rpt(op.arpt, op.a64, ar);
     const int64_t p1 = ld_rpt(op.arpt, op.a64, ar + 1);
     const int S = pick_lanes(w.lanes, w.crpt[row], p1 - p0, 32);
-    const int nsub = kBmBlock / S, sub = threadIdx.x / S, ls = threadIdx.x % S;
     const int64_t span = static_cast<int64_t>(words) * 32;
     long long total = 0;
     for (int64_t c0 = 0; c0 < op.ncols; c0 += span) {
         const int nw = static_cast<int>(((op.ncols - c0 < span ? op.ncols - c0 : span) + 31) / 32);
         for (int i = threadIdx.x; i < nw; i += kBmBlock) bm[i] = 0u;
         __syncthreads();
-        for (int64_t p = p0 + sub; p < p1; p += nsub) {
-            const int k = __ldg(op.acol + p);
-            const int64_t q1 = ld_rpt(op.brpt, op.b64, k + 1);
-            for (int64_t q = ld_rpt(op.brpt, op.b64, k) + ls; q < q1; q += S) {
-                const int64_t rel = static_cast<int64_t>(__ldg(op.bcol + q)) - c0;
-                if (rel >= 0 && rel < span)
-                    atomicOr(bm + (rel >> 5), 1u << (rel & 31));
-            }
-        }
-        __syncthreads();
+        block_row_walk<kBmBlock, false>(op, p0, p1, S, sc, [&](int key, double, long long) {
+            const int64_t rel = static_cast<int64_t>(key) - c0;
+            if (rel >= 0 && rel < span) atomicOr(bm + (rel >> 5), 1u << (rel & 31));
+        });
         for (int i = threadIdx.x; i < nw; i += kBmBlock) total += __popc(bm[i]);
         __syncthreads();
     }
@@ -130,8 +136,10 @@ struct SymEntry {
     SymFn fn;
 };
 
-#define SYM_ENTRY(TPR, BLOCK, T) \
-    {{TPR, BLOCK, T, T, 0, sizeof(int) * (BLOCK / TPR) * (size_t)T}, &sym_hash_kernel<TPR, BLOCK, T>},
+#define SYM_ENTRY(TPR, BLOCK, T)                                                        \
+    {{TPR, BLOCK, T, T, 0,                                                              \
+      sizeof(int) * (BLOCK / TPR) * (size_t)T + (TPR > 32 ? sizeof(WalkScratch) : 0)}, \
+     &sym_hash_kernel<TPR, BLOCK, T>},
 
 static SymEntry g_sym[] = {SYM_TABLE(SYM_ENTRY)};
 static constexpr int kSymHash = sizeof(g_sym) / sizeof(g_sym[0]);
@@ -152,7 +160,7 @@ cudaError_t sym_prepare(int smem_optin) {
                                              static_cast<int>(g_sym[i].d.smem));
         if (e != cudaSuccess) return e;
     }
-    g_sym_bitmap.table = static_cast<long long>(smem_optin / 4) * 32;
+    g_sym_bitmap.table = static_cast<long long>((smem_optin - sizeof(WalkScratch)) / 4) * 32;
     return cudaFuncSetAttribute(reinterpret_cast<const void *>(&sym_bitmap_kernel),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
 }
@@ -167,7 +175,8 @@ cudaError_t launch_sym(int id, const Operands &op, const BinWork &w, size_t smem
         g_sym[id].fn<<<static_cast<unsigned>(grid), d.block, d.smem, s>>>(op, w);
     } else {
         const int words = static_cast<int>(smem_bitmap / 4);
-        sym_bitmap_kernel<<<static_cast<unsigned>(w.cnt), kBmBlock, smem_bitmap, s>>>(op, w, words);
+        sym_bitmap_kernel<<<static_cast<unsigned>(w.cnt), kBmBlock, smem_bitmap + sizeof(WalkScratch), s>>>(
+            op, w, words);
     }
     return cudaGetLastError();
 }
