@@ -201,6 +201,38 @@ int spgemm_kernel_info(int phase, int id, int32_t *threads_per_row,
 
 const char *spgemm_strerror(int code);
 
+/* ---- Sizing C without allocating device memory --------------------------
+ * The paper has no counterpart to this function; it serves callers that
+ * cannot call cudaMalloc at run time, such as a serving loop whose device
+ * memory is all owned by another framework's allocator, a runtime with a
+ * memory budget fixed at start-up, or code that is itself an allocator.
+ *
+ * spgemm_rowptr_noalloc runs the symbolic phase of C = A * B over all rows
+ * of A (n_prod, symbolic binning, the symbolic kernels, the exclusive scan)
+ * and writes C's int64 row pointer into crpt (device memory, A->rows + 1
+ * entries, caller-owned): crpt[i] is the offset of row i, crpt[A->rows] =
+ * *nnzC (nnzC may be NULL). A->val and B->val are not read. The result is
+ * the same row pointer that spgemm_symbolic followed by spgemm_numeric
+ * produce with the default configuration.
+ *
+ * It allocates nothing and creates no handle, stream or event: its scratch
+ * memory is one fixed array inside the library (about 4 MB, held by every
+ * GPU that loads the library until the process exits), sized for at most
+ * SPGEMM_NOALLOC_MAX_ROWS rows of A; larger A is rejected with
+ * SPGEMM_ERR_INVALID. All work is ordered on `stream` (a cudaStream_t; NULL
+ * = legacy default stream) and the call waits for it twice (to read the
+ * bin sizes and the total).
+ *
+ * The first call on a device looks up the array's device address and
+ * prepares the kernels on that device, with that device current; make that
+ * first call before any stream capture. Every call uses the same array and
+ * it keeps the previous call's contents (the call clears what must start at
+ * zero), so calls that overlap on the GPU, from several host threads or on
+ * several streams, race with each other and must be serialised by the
+ * caller. */
+#define SPGEMM_NOALLOC_MAX_ROWS (1 << 20)
+int spgemm_rowptr_noalloc(const spgemm_csr_in *A, const spgemm_csr_in *B,
+                          int64_t *crpt, void *stream, int64_t *nnzC);
 
 #ifdef __cplusplus
 }

@@ -21,6 +21,7 @@ EXPORTS = [
     "spgemm_numeric", "spgemm_multiply", "spgemm_status", "spgemm_free",
     "spgemm_destroy", "spgemm_last_stats", "spgemm_kernel_info", "spgemm_strerror",
     "spgemm_multiply_host", "spgemm_bin_stats", "spgemm_set_timing", "spgemm_kernel_times",
+    "spgemm_rowptr_noalloc",
 ]
 
 
@@ -86,6 +87,7 @@ def lib(path: str | None = None):
             "spgemm_multiply_host": [P, P, P, I64, SINK_FN, P, ctypes.POINTER(I64)],
             "spgemm_bin_stats": [P, ctypes.c_int, ctypes.POINTER(I64), ctypes.c_int],
             "spgemm_set_timing": [P, ctypes.c_int],
+            "spgemm_rowptr_noalloc": [P, P, P, P, ctypes.POINTER(I64)],
             "spgemm_kernel_times": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64),
                                     ctypes.c_int, ctypes.c_int],
         }
