@@ -43,8 +43,10 @@ WORKLOADS = {
                       "diagonal 27, seed 3", lambda: W.stencil27(128, seed=3)),
     "laplace2d_64": ("C = A*A, A = 5-point Laplacian on 64x64 (4 / -1)",
                      lambda: W.laplacian_2d(64)),
-    "rmat18": ("C = A*A, A = R-MAT n=2^18, degree 16, seed 1 (small profiling case)",
+    "rmat18": ("C = A*A, A = R-MAT n=2^18, degree 16, seed 1",
                lambda: W.rmat(18, 16, seed=1)),
+    "rmat16": ("C = A*A, A = R-MAT n=2^16, degree 16, seed 1 (small profiling case)",
+               lambda: W.rmat(16, 16, seed=1)),
 }
 
 SLOT_NAMES = ([f"sym_bin{j}" for j in range(16)] + [f"num_bin{j}" for j in range(16)]
@@ -209,6 +211,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-products", type=float, default=1.5e9)
     ap.add_argument("--config", default=None, help="bin configuration JSON file")
+    ap.add_argument("--autotune", action="store_true",
+                    help="also tune the bin configuration and time plain vs tuned")
+    ap.add_argument("--save-config", default=None)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not os.environ.get("BENCH_ALLOW_SHORT"):
         args.warmup = 3
@@ -336,6 +341,23 @@ def main():
     breakdown = {SLOT_NAMES[i]: round(kms[i] / args.steps, 3) for i in range(len(kms)) if kms[i] > 0}
     gpu_launches = int(sum(kln) + kln[37])   # the scan slot covers two kernels
 
+    bins = {"sym_rows": list(bins_sym)[:16], "sym_nprod": list(bins_sym)[16:32],
+            "num_rows": list(bins_num)[:16], "num_nnz": list(bins_num)[16:32]}
+    cfg_used = h.get_config()
+
+    tuned = None
+    if args.autotune and rank == 0:
+        from paper_2206_07244_gb300 import autotune
+        best, hist = autotune.tune(dA, dA, reps=2)
+        t_best = autotune.time_config(dA, dA, best, reps=3)
+        t_plain = autotune.time_config(dA, dA, None or cfg_used, reps=3)
+        tuned = {"plain_ms": round(t_plain, 3), "tuned_ms": round(t_best, 3),
+                 "plain_gflops": round(2.0 * nprod_slab / (t_plain / 1e3) / 1e9, 3),
+                 "tuned_gflops": round(2.0 * nprod_slab / (t_best / 1e3) / 1e9, 3),
+                 "config": best, "trials": len(hist)}
+        if args.save_config:
+            json.dump(best, open(args.save_config, "w"))
+
     e2e = None
     if not args.no_e2e and rank == 0:
         e2e = run_e2e(A, lib, args.e2e_steps, nprod_slab if ws == 1 else None)
@@ -357,6 +379,7 @@ def main():
                            "bin_config": "autotuned" if args.config else "default"},
                 "roofline": roofline, "roofline_whole_step": whole,
                 "stage_ms_live": breakdown, "kernel_ms_serial": serial,
+                "bins": bins, "autotune": tuned,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)

@@ -1,0 +1,111 @@
+"""Autotuner for the bin configuration of the plain two-phase path.
+
+The paper fixes its bin ranges by experiment (Sec. 5.7; Tables 4 and 5 try
+tables 1x/1.2x/1.5x larger than the largest n_prod of a symbolic bin and
+1x/1.5x/2x/3x larger than the largest n_nz of a numeric bin). Here the same
+choices, plus two that GB300's 227 KB per block opens up, are searched per
+workload by timing the library itself:
+
+- ``ratio``: table size / largest row size of each hash bin, per phase;
+- ``cut``: the last hash kernel kept in a phase; larger rows go to the
+  shared-memory bitmap kernel (whose cost per row grows with the number of
+  columns rather than with the row);
+- ``lanes_per_brow``: automatic per row, or fixed.
+
+The search is coordinate descent from the defaults; each candidate is timed
+with CUDA events over a few whole multiplies. The result is a plain dict
+(JSON-serialisable) for ``Handle(config)`` or ``bench.py --config``.
+"""
+
+from __future__ import annotations
+
+import json
+import math
+
+from . import CSR, Handle, kernel_table
+
+SYM_RATIOS = (1.0, 1.2, 1.5)
+NUM_RATIOS = (1.0, 1.5, 2.0, 3.0)
+
+
+def make_config(sym_ratio=1.2, num_ratio=2.0, sym_cut=None, num_cut=None, lanes=0) -> dict:
+    """A bin configuration: hash kernels 0..cut of each phase with ranges
+    floor(table / ratio) (capped at the kernel's capacity), then the bitmap
+    kernel for everything larger."""
+    cfg = {"lanes_per_brow": int(lanes)}
+    for key, phase, ratio, cut in (("sym", 0, sym_ratio, sym_cut), ("num", 1, num_ratio, num_cut)):
+        table = kernel_table(phase)
+        bitmap = len(table) - 1
+        last = bitmap - 1 if cut is None else min(int(cut), bitmap - 1)
+        kernels, ranges = [], []
+        prev = -1
+        for k in range(last + 1):
+            tpr, blk, tab, cap = table[k]
+            r = min(int(math.floor(tab / ratio)), cap)
+            if r <= prev:
+                continue
+            kernels.append(k)
+            ranges.append(r)
+            prev = r
+        kernels.append(bitmap)
+        ranges.append(-1)
+        cfg[f"{key}_kernel"] = kernels
+        cfg[f"{key}_range"] = ranges
+    return cfg
+
+
+def time_config(A: CSR, B: CSR, cfg: dict, reps: int = 3, warmup: int = 1) -> float:
+    """Median milliseconds of one whole multiply with this configuration."""
+    import torch
+    with Handle(cfg) as h:
+        for _ in range(warmup):
+            C = h.multiply(A, B)
+            del C
+        times = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            C = h.multiply(A, B)
+            e1.record()
+            e1.synchronize()
+            del C
+            times.append(e0.elapsed_time(e1))
+        h.status()
+    times.sort()
+    return times[len(times) // 2]
+
+
+def tune(A: CSR, B: CSR, reps: int = 3, log=None) -> tuple[dict, list]:
+    """Coordinate descent over (num_cut, num_ratio, sym_cut, sym_ratio,
+    lanes). Returns (best configuration, [(params, ms), ...])."""
+    nsym = len(kernel_table(0)) - 1
+    nnum = len(kernel_table(1)) - 1
+    params = {"sym_ratio": 1.2, "num_ratio": 2.0, "sym_cut": nsym - 1, "num_cut": nnum - 1,
+              "lanes": 0}
+    space = {
+        "num_cut": list(range(max(0, nnum - 6), nnum)),
+        "num_ratio": list(NUM_RATIOS),
+        "sym_cut": list(range(max(0, nsym - 5), nsym)),
+        "sym_ratio": list(SYM_RATIOS),
+        "lanes": [0, 8, 32],
+    }
+    seen = {}
+
+    def measure(p):
+        key = json.dumps(p, sort_keys=True)
+        if key not in seen:
+            seen[key] = time_config(A, B, make_config(**p), reps=reps)
+            if log:
+                log(f"{p} -> {seen[key]:.3f} ms")
+        return seen[key]
+
+    best = measure(params)
+    for name in ("num_cut", "num_ratio", "sym_cut", "sym_ratio", "lanes"):
+        for v in space[name]:
+            cand = dict(params, **{name: v})
+            t = measure(cand)
+            if t < best:
+                best, params = t, cand
+    history = [(json.loads(k), v) for k, v in seen.items()]
+    return make_config(**params), history

@@ -52,16 +52,21 @@ __device__ __forceinline__ uint32_t next_slot(uint32_t h) {
     else return (h + 1 == static_cast<uint32_t>(T)) ? 0u : h + 1;
 }
 
-// Threads that walk one B row together: a power of two no larger than the
-// row group, chosen from the mean length of the referenced B rows unless
-// the configuration fixes it.
+// Products one lane loads together before using them (a piece of a B row
+// is at most kPieceIters * S long for S lanes).
+constexpr int kPieceIters = 4;
+
+// Threads that walk one B row together: the smallest power of two S for
+// which S * kPieceIters covers the mean length of the referenced B rows (so
+// every lane keeps kPieceIters loads in flight), no larger than the row
+// group or a warp, unless the configuration fixes it.
 __device__ __forceinline__ int pick_lanes(int fixed, int64_t nprod, int64_t nnza, int group) {
     int cap = group < 32 ? group : 32;
     if (fixed > 0) return fixed < cap ? fixed : cap;
     if (nnza <= 0) return 1;
     int64_t mean = (nprod + nnza - 1) / nnza;
     int s = 1;
-    while (s < mean && s < cap) s <<= 1;
+    while (static_cast<int64_t>(s) * kPieceIters < mean && s < cap) s <<= 1;
     return s;
 }
 
@@ -164,7 +169,6 @@ namespace ops {
 // lanes take pieces round-robin; a sub-group's lanes read a piece with unit
 // stride (coalesced). The piece -> A entry map is a binary search over the
 // chunk's piece offsets in shared memory, paid once per piece.
-constexpr int kPieceIters = 4;
 constexpr int kWalkChunk = 256;
 
 struct WalkScratch {
@@ -209,9 +213,12 @@ __device__ __forceinline__ long long block_excl_scan_ll(long long x, long long &
     }
 }
 
-// Calls f(key, a_value, q) for every product of the row [p0, p1) of A.
-// Every thread of the block must call it (it synchronises the block).
-template <int BLOCK, bool NEED_A, typename F>
+// Calls f(key, a_value, b_value) for every product of the row [p0, p1) of A
+// (a_value and b_value only when NEED_VAL). Every thread of the block must
+// call it (it synchronises the block). A lane's products of one piece (at
+// most kPieceIters) are loaded together before any of them is used, so each
+// thread keeps several L2 loads in flight.
+template <int BLOCK, bool NEED_VAL, typename F>
 __device__ __forceinline__ void block_row_walk(const Operands &op, int64_t p0, int64_t p1, int S,
                                                WalkScratch *sc, F &&f) {
     static_assert(BLOCK >= 32 && BLOCK % 32 == 0, "block walk needs whole warps");
@@ -229,7 +236,7 @@ __device__ __forceinline__ void block_row_walk(const Operands &op, int64_t p0, i
                 const long long len = ld_rpt(op.brpt, op.b64, k + 1) - q0;
                 sc->q0[t] = q0;
                 sc->len[t] = static_cast<int>(len);
-                if (NEED_A) sc->a[t] = __ldg(op.aval + c + t);
+                if (NEED_VAL) sc->a[t] = __ldg(op.aval + c + t);
                 pieces = (len + W - 1) / W;
             }
         }
@@ -245,13 +252,75 @@ __device__ __forceinline__ void block_row_walk(const Operands &op, int64_t p0, i
                 if (sc->pstart[mid] <= it) lo = mid; else hi = mid;
             }
             const long long piece = it - sc->pstart[lo];
-            const long long qb = sc->q0[lo] + piece * W;
+            const long long qb = sc->q0[lo] + piece * W + ls;
             const long long qe0 = sc->q0[lo] + sc->len[lo];
-            const long long qe = qb + W < qe0 ? qb + W : qe0;
-            const double a = NEED_A ? sc->a[lo] : 0.0;
-            for (long long q = qb + ls; q < qe; q += S) f(__ldg(op.bcol + q), a, q);
+            const double a = NEED_VAL ? sc->a[lo] : 0.0;
+            int key[kPieceIters];
+            double bv[kPieceIters];
+#pragma unroll
+            for (int u = 0; u < kPieceIters; ++u) {
+                const long long q = qb + static_cast<long long>(u) * S;
+                key[u] = q < qe0 ? __ldg(op.bcol + q) : -1;
+                bv[u] = (NEED_VAL && q < qe0) ? __ldg(op.bval + q) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kPieceIters; ++u)
+                if (key[u] >= 0) f(key[u], a, bv[u]);
         }
         __syncthreads();
+    }
+}
+
+}  // namespace ops
+
+namespace ops {
+
+// Row walk for row groups of TPR <= 32 lanes (a slice of one warp). The
+// group loads TPR A entries at once into registers (one per lane), then its
+// sub-groups of S lanes take entries round-robin and read each B row in
+// pieces of kPieceIters * S products, every lane loading its kPieceIters
+// products before using them. Entry data moves between the group's lanes by
+// shuffles under the group's own lane mask: groups of one warp may pick
+// different S and run different trip counts. S must be the same on every
+// lane of a group. Calls f(key, a_value, b_value).
+template <int TPR, bool NEED_VAL, typename F>
+__device__ __forceinline__ void group_row_walk(const Operands &op, int64_t p0, int64_t p1, int S,
+                                               F &&f) {
+    static_assert(TPR <= 32, "group walk is for sub-warp row groups");
+    const unsigned gm = group_mask<TPR>();
+    const int lg = threadIdx.x % TPR;
+    const int gbase = (threadIdx.x & 31) - lg;     // first lane of this group in the warp
+    const int nsub = TPR / S, sub = lg / S, ls = lg % S;
+    const int64_t n = p1 - p0;
+    for (int64_t c = 0; c < n; c += TPR) {
+        long long my_q0 = 0;
+        int my_len = 0;
+        double my_a = 0.0;
+        if (c + lg < n) {
+            const int k = __ldg(op.acol + p0 + c + lg);
+            my_q0 = ld_rpt(op.brpt, op.b64, k);
+            my_len = static_cast<int>(ld_rpt(op.brpt, op.b64, k + 1) - my_q0);
+            if (NEED_VAL) my_a = __ldg(op.aval + p0 + c + lg);
+        }
+        for (int e0 = 0; e0 < TPR; e0 += nsub) {
+            const int src = gbase + e0 + sub;
+            const long long q0 = __shfl_sync(gm, my_q0, src);
+            const int len = __shfl_sync(gm, my_len, src);
+            const double a = NEED_VAL ? __shfl_sync(gm, my_a, src) : 0.0;
+            for (int off = ls; off < len; off += S * kPieceIters) {
+                int key[kPieceIters];
+                double bv[kPieceIters];
+#pragma unroll
+                for (int u = 0; u < kPieceIters; ++u) {
+                    const int o = off + u * S;
+                    key[u] = o < len ? __ldg(op.bcol + q0 + o) : -1;
+                    bv[u] = (NEED_VAL && o < len) ? __ldg(op.bval + q0 + o) : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < kPieceIters; ++u)
+                    if (key[u] >= 0) f(key[u], a, bv[u]);
+            }
+        }
     }
 }
 

@@ -59,9 +59,13 @@ __device__ __forceinline__ int numeric_lanes(const Operands &op, int fixed, int6
 
 // Minimum resident blocks: enough for 2048 threads per SM (<= 32 registers
 // per thread, Sec. 5.6) unless the table is so large that one block fills
-// the SM's shared memory anyway.
+// the SM's shared memory anyway. Sub-warp row groups keep four products in
+// flight per lane (values included), which needs up to 40 registers: they
+// take 1536 threads per SM instead of spilling.
 template <int TPR, int BLOCK, int T>
-__global__ void __launch_bounds__(BLOCK, (T * 12 * (BLOCK / TPR) > 110 * 1024) ? 1 : 2048 / BLOCK)
+__global__ void __launch_bounds__(BLOCK, (T * 12 * (BLOCK / TPR) > 110 * 1024)
+                                             ? 1
+                                             : (TPR <= 32 ? 1536 / BLOCK : 2048 / BLOCK))
 num_hash_kernel(Operands op, BinWork w) {
     constexpr int RPB = BLOCK / TPR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -93,18 +97,13 @@ num_hash_kernel(Operands op, BinWork w) {
         // one row per block: flattened walk over B-row pieces
         WalkScratch *sc = reinterpret_cast<WalkScratch *>(
             smem_raw + (sizeof(int) + sizeof(double)) * (size_t)RPB * T);
-        block_row_walk<BLOCK, true>(op, p0, p1, S, sc, [&](int key, double a, long long q) {
-            num_insert<T>(tk, tv, key, a * __ldg(op.bval + q), w.err);
+        block_row_walk<BLOCK, true>(op, p0, p1, S, sc, [&](int key, double a, double b) {
+            num_insert<T>(tk, tv, key, a * b, w.err);
         });
     } else {
-        const int nsub = TPR / S, sub = lg / S, ls = lg % S;
-        for (int64_t p = p0 + sub; p < p1; p += nsub) {
-            const int k = __ldg(op.acol + p);
-            const double a = __ldg(op.aval + p);
-            const int64_t q1 = ld_rpt(op.brpt, op.b64, k + 1);
-            for (int64_t q = ld_rpt(op.brpt, op.b64, k) + ls; q < q1; q += S)
-                num_insert<T>(tk, tv, __ldg(op.bcol + q), a * __ldg(op.bval + q), w.err);
-        }
+        group_row_walk<TPR, true>(op, p0, p1, S, [&](int key, double a, double b) {
+            num_insert<T>(tk, tv, key, a * b, w.err);
+        });
     }
     group_sync<TPR>();
     // condense: occupied slots move to the front, chunk by chunk; a write
@@ -221,19 +220,27 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
         // pass 1: the row's columns inside this window. 32-bit atomics on the
         // two halves of a 64-bit word: shared 64-bit atomics run several
         // times slower on this GPU
-        block_row_walk<kBmBlock, false>(op, p0, p1, S, sc, [&](int key, double, long long) {
+        block_row_walk<kBmBlock, false>(op, p0, p1, S, sc, [&](int key, double, double) {
             const int64_t rel = static_cast<int64_t>(key) - c0;
             if (rel >= 0 && rel < span) atomicOr(bm32 + (rel >> 5), 1u << (rel & 31));
         });
-        // per-word prefix counts = rank of a word's first column in the window
+        // per-word prefix counts = rank of a word's first column in the
+        // window; thread t owns a contiguous run of words, so one block scan
+        // of the per-thread counts suffices
         unsigned run = 0;
-        for (int b = 0; b < nw; b += kBmBlock) {
-            const int i = b + static_cast<int>(threadIdx.x);
-            const unsigned c = i < nw ? static_cast<unsigned>(__popcll(bm[i])) : 0u;
+        {
+            const int per = (nw + kBmBlock - 1) / kBmBlock;
+            const int i0 = static_cast<int>(threadIdx.x) * per;
+            const int i1 = i0 + per < nw ? i0 + per : nw;
+            unsigned c = 0;
+            for (int i = i0; i < i1; ++i) c += static_cast<unsigned>(__popcll(bm[i]));
             unsigned tot;
-            const unsigned ex = block_excl_scan(c, tot, sw);
-            if (i < nw) pre[i] = run + ex;
-            run += tot;
+            unsigned ex = block_excl_scan(c, tot, sw);
+            for (int i = i0; i < i1; ++i) {
+                pre[i] = ex;
+                ex += static_cast<unsigned>(__popcll(bm[i]));
+            }
+            run = tot;
         }
         __syncthreads();
         const int64_t cnt = run;
@@ -254,14 +261,14 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
             for (int64_t t = threadIdx.x; t < cnt; t += kBmBlock) cval[t] = 0.0;
             __syncthreads();
             // pass 2: each product lands on its column's rank
-            block_row_walk<kBmBlock, true>(op, p0, p1, S, sc, [&](int key, double a, long long q) {
+            block_row_walk<kBmBlock, true>(op, p0, p1, S, sc, [&](int key, double a, double b) {
                 const int64_t rel = static_cast<int64_t>(key) - c0;
                 if (rel >= 0 && rel < span) {
                     const int wi = static_cast<int>(rel >> 6);
                     const int bi = static_cast<int>(rel & 63);
                     const unsigned rank = pre[wi] +
                         static_cast<unsigned>(__popcll(bm[wi] & ((1ull << bi) - 1ull)));
-                    atomicAdd(cval + rank, a * __ldg(op.bval + q));
+                    atomicAdd(cval + rank, a * b);
                 }
             });
         }

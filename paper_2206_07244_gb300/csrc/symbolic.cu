@@ -66,21 +66,23 @@ sym_hash_kernel(Operands op, BinWork w) {
         const int64_t p0 = ld_rpt(op.arpt, op.a64, ar);
         const int64_t p1 = ld_rpt(op.arpt, op.a64, ar + 1);
         const int S = pick_lanes(w.lanes, w.crpt[row], p1 - p0, 32);
-        block_row_walk<BLOCK, false>(op, p0, p1, S, sc, [&](int key, double, long long) {
+        block_row_walk<BLOCK, false>(op, p0, p1, S, sc, [&](int key, double, double) {
             cnt += sym_insert<T>(tab, key, w.err);
         });
-    } else if (valid) {
-        const int64_t ar = op.row0 + row;
-        const int64_t p0 = ld_rpt(op.arpt, op.a64, ar);
-        const int64_t p1 = ld_rpt(op.arpt, op.a64, ar + 1);
-        const int S = pick_lanes(w.lanes, w.crpt[row], p1 - p0, TPR);
-        const int nsub = TPR / S, sub = lg / S, ls = lg % S;
-        for (int64_t p = p0 + sub; p < p1; p += nsub) {
-            const int k = __ldg(op.acol + p);
-            const int64_t q1 = ld_rpt(op.brpt, op.b64, k + 1);
-            for (int64_t q = ld_rpt(op.brpt, op.b64, k) + ls; q < q1; q += S)
-                cnt += sym_insert<T>(tab, __ldg(op.bcol + q), w.err);
+    } else {
+        int64_t p0 = 0, p1 = 0;
+        int S = 1;
+        if (valid) {
+            const int64_t ar = op.row0 + row;
+            p0 = ld_rpt(op.arpt, op.a64, ar);
+            p1 = ld_rpt(op.arpt, op.a64, ar + 1);
+            S = pick_lanes(w.lanes, w.crpt[row], p1 - p0, TPR);
         }
+        // lanes of one group must agree on S: take the group's lane-0 value
+        S = __shfl_sync(0xffffffffu, S, (threadIdx.x & 31) - lg);
+        group_row_walk<TPR, false>(op, p0, p1, S, [&](int key, double, double) {
+            cnt += sym_insert<T>(tab, key, w.err);
+        });
     }
     cnt = group_sum<TPR>(cnt, red);
     if (valid && lg == 0) w.crpt[row] = cnt;
@@ -106,7 +108,7 @@ sym_bitmap_kernel(Operands op, BinWork w, int words) {
         const int nw = static_cast<int>(((op.ncols - c0 < span ? op.ncols - c0 : span) + 31) / 32);
         for (int i = threadIdx.x; i < nw; i += kBmBlock) bm[i] = 0u;
         __syncthreads();
-        block_row_walk<kBmBlock, false>(op, p0, p1, S, sc, [&](int key, double, long long) {
+        block_row_walk<kBmBlock, false>(op, p0, p1, S, sc, [&](int key, double, double) {
             const int64_t rel = static_cast<int64_t>(key) - c0;
             if (rel >= 0 && rel < span) atomicOr(bm + (rel >> 5), 1u << (rel & 31));
         });
