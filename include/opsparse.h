@@ -80,11 +80,17 @@ typedef void (*spgemm_free_fn)(void *ptr, void *stream, void *ctx);
  * phase) is <= range[j] and > range[j-1] (Algorithm 1: first j with
  * size <= r_range[j]); the last used bin must have range -1 (no bound).
  * kernel[j] picks the kernel that computes bin j from the table printed by
- * spgemm_kernel_info(); its capacity must hold range[j]. nbins = 0 in a
- * phase selects the library's defaults for this device.
- * lanes_per_brow: threads that walk one row of B together (1..32, a power
- * of two), or 0 to pick it per output row from the mean referenced B-row
- * length. */
+ * spgemm_kernel_info(); its capacity must hold range[j]. A handle created
+ * with cfg NULL (or reset with spgemm_set_config(h, NULL)) uses the default
+ * bins, every hash kernel with tables 1.2x (symbolic) and 2x (numeric) the
+ * largest row of the bin (Sec. 5.7), and moves the switch to the bitmap
+ * kernels with the number of columns of B at each spgemm_symbolic; the
+ * configuration then in use is what spgemm_get_config returns.
+ * lanes_per_brow / num_lanes_per_brow: threads that walk one row of B
+ * together in the symbolic / numeric phase (1..32, a power of two), or 0 to
+ * pick it per output row from the mean referenced B-row length.
+ * bitmap_unroll: products each thread of a bitmap kernel loads before using
+ * them (4 or 8; 0 = 4). */
 typedef struct {
     int32_t sym_nbins;
     int32_t sym_kernel[SPGEMM_MAX_BINS];
@@ -93,7 +99,9 @@ typedef struct {
     int32_t num_kernel[SPGEMM_MAX_BINS];
     int64_t num_range[SPGEMM_MAX_BINS];
     int32_t lanes_per_brow;
-    int32_t reserved[7];
+    int32_t num_lanes_per_brow;
+    int32_t bitmap_unroll;
+    int32_t reserved[5];
 } spgemm_config;
 
 typedef struct spgemm_handle spgemm_handle;

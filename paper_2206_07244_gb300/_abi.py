@@ -47,7 +47,8 @@ class Config(ctypes.Structure):
                 ("sym_range", ctypes.c_int64 * MAX_BINS),
                 ("num_nbins", ctypes.c_int32), ("num_kernel", ctypes.c_int32 * MAX_BINS),
                 ("num_range", ctypes.c_int64 * MAX_BINS),
-                ("lanes_per_brow", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("lanes_per_brow", ctypes.c_int32), ("num_lanes_per_brow", ctypes.c_int32),
+                ("bitmap_unroll", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -126,7 +127,9 @@ def config_to_dict(c: Config) -> dict:
             "sym_range": list(c.sym_range[:c.sym_nbins]),
             "num_kernel": list(c.num_kernel[:c.num_nbins]),
             "num_range": list(c.num_range[:c.num_nbins]),
-            "lanes_per_brow": int(c.lanes_per_brow)}
+            "lanes_per_brow": int(c.lanes_per_brow),
+            "num_lanes_per_brow": int(c.num_lanes_per_brow),
+            "bitmap_unroll": int(c.bitmap_unroll)}
 
 
 def config_from_dict(d: dict) -> Config:
@@ -142,4 +145,6 @@ def config_from_dict(d: dict) -> Config:
     for j, (k, r) in enumerate(zip(nk, nr)):
         c.num_kernel[j], c.num_range[j] = int(k), int(r)
     c.lanes_per_brow = int(d.get("lanes_per_brow", 0))
+    c.num_lanes_per_brow = int(d.get("num_lanes_per_brow", 0))
+    c.bitmap_unroll = int(d.get("bitmap_unroll", 0))
     return c

@@ -10,7 +10,9 @@ workload by timing the library itself:
 - ``cut``: the last hash kernel kept in a phase; larger rows go to the
   shared-memory bitmap kernel (whose cost per row grows with the number of
   columns rather than with the row);
-- ``lanes_per_brow``: automatic per row, or fixed.
+- ``lanes_per_brow`` / ``num_lanes_per_brow``: threads per B row in each
+  phase, automatic per row or fixed;
+- ``bitmap_unroll``: products each bitmap-kernel thread keeps in flight.
 
 The search is coordinate descent from the defaults; each candidate is timed
 with CUDA events over a few whole multiplies. The result is a plain dict
@@ -28,11 +30,13 @@ SYM_RATIOS = (1.0, 1.2, 1.5)
 NUM_RATIOS = (1.0, 1.5, 2.0, 3.0)
 
 
-def make_config(sym_ratio=1.2, num_ratio=2.0, sym_cut=None, num_cut=None, lanes=0) -> dict:
+def make_config(sym_ratio=1.2, num_ratio=2.0, sym_cut=None, num_cut=None, lanes=0,
+                num_lanes=0, unroll=0) -> dict:
     """A bin configuration: hash kernels 0..cut of each phase with ranges
     floor(table / ratio) (capped at the kernel's capacity), then the bitmap
-    kernel for everything larger."""
-    cfg = {"lanes_per_brow": int(lanes)}
+    kernel for everything larger; threads per B row for each phase."""
+    cfg = {"lanes_per_brow": int(lanes), "num_lanes_per_brow": int(num_lanes),
+           "bitmap_unroll": int(unroll)}
     for key, phase, ratio, cut in (("sym", 0, sym_ratio, sym_cut), ("num", 1, num_ratio, num_cut)):
         table = kernel_table(phase)
         bitmap = len(table) - 1
@@ -82,13 +86,15 @@ def tune(A: CSR, B: CSR, reps: int = 3, log=None) -> tuple[dict, list]:
     nsym = len(kernel_table(0)) - 1
     nnum = len(kernel_table(1)) - 1
     params = {"sym_ratio": 1.2, "num_ratio": 2.0, "sym_cut": nsym - 1, "num_cut": nnum - 1,
-              "lanes": 0}
+              "lanes": 0, "num_lanes": 0, "unroll": 0}
     space = {
         "num_cut": list(range(max(0, nnum - 6), nnum)),
         "num_ratio": list(NUM_RATIOS),
         "sym_cut": list(range(max(0, nsym - 5), nsym)),
         "sym_ratio": list(SYM_RATIOS),
         "lanes": [0, 8, 32],
+        "num_lanes": [0, 8, 32],
+        "unroll": [0, 8],
     }
     seen = {}
 
@@ -101,7 +107,7 @@ def tune(A: CSR, B: CSR, reps: int = 3, log=None) -> tuple[dict, list]:
         return seen[key]
 
     best = measure(params)
-    for name in ("num_cut", "num_ratio", "sym_cut", "sym_ratio", "lanes"):
+    for name in ("num_cut", "num_ratio", "sym_cut", "sym_ratio", "lanes", "num_lanes", "unroll"):
         for v in space[name]:
             cand = dict(params, **{name: v})
             t = measure(cand)

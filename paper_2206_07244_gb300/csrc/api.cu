@@ -60,6 +60,7 @@ struct spgemm_handle {
     void *ctx = nullptr;
     cudaMemPool_t pool = nullptr;
     spgemm_config cfg{};
+    bool cfg_auto = false;   // default configuration: hash/bitmap cut derived per call from N
     // scratch arena: [Counters sym | Counters num | err] [bins] [tile sums]
     unsigned char *arena = nullptr;
     size_t arena_bytes = 0;
@@ -172,7 +173,9 @@ long long *d_tiles(spgemm_handle *h) {
 bool is_pow2_lanes(int x) { return x == 0 || x == 1 || x == 2 || x == 4 || x == 8 || x == 16 || x == 32; }
 
 int validate_config(const spgemm_config &c) {
-    if (!is_pow2_lanes(c.lanes_per_brow)) return SPGEMM_ERR_INVALID;
+    if (!is_pow2_lanes(c.lanes_per_brow) || !is_pow2_lanes(c.num_lanes_per_brow))
+        return SPGEMM_ERR_INVALID;
+    if (c.bitmap_unroll != 0 && c.bitmap_unroll != 4 && c.bitmap_unroll != 8) return SPGEMM_ERR_INVALID;
     for (int phase = 0; phase < 2; ++phase) {
         const int nb = phase ? c.num_nbins : c.sym_nbins;
         const int32_t *k = phase ? c.num_kernel : c.sym_kernel;
@@ -216,6 +219,31 @@ void default_config(spgemm_config &c) {
         c.num_range[j] = d.bitmap ? -1 : static_cast<int64_t>(d.table / 2);
     }
     c.lanes_per_brow = 0;
+}
+
+// The default configuration adapts where large rows leave the hash bins
+// for the bitmap kernels to the number of columns N: a bitmap kernel clears
+// and scans N bits per row (N/64 words with rank counts in the numeric
+// phase), so its fixed cost per row grows with N while a hash bin's
+// condense/sort cost grows with the row. Measured on GB300 (R-MAT n = 2^16,
+// 2^18, 2^20), numeric rows above max(1024, N/512) entries and symbolic rows
+// above max(6826, N/128) products run faster in the bitmap kernels.
+void auto_cut(spgemm_config &c, int64_t ncols) {
+    default_config(c);
+    const int64_t num_lim = std::max<int64_t>(1024, ncols / 512);
+    const int64_t sym_lim = std::max<int64_t>(6826, ncols / 128);
+    for (int phase = 0; phase < 2; ++phase) {
+        int32_t *k = phase ? c.num_kernel : c.sym_kernel;
+        int64_t *r = phase ? c.num_range : c.sym_range;
+        int32_t &nb = phase ? c.num_nbins : c.sym_nbins;
+        const int64_t lim = phase ? num_lim : sym_lim;
+        int keep = 0;
+        while (keep < nb - 1 && r[keep] <= lim) ++keep;
+        if (keep == 0) keep = 1;  // always keep the smallest hash bin
+        k[keep] = k[nb - 1];      // the bitmap kernel takes everything larger
+        r[keep] = -1;
+        nb = keep + 1;
+    }
 }
 
 int cuda_rc(cudaError_t e) {
@@ -263,7 +291,8 @@ int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *s
         w.off = identity ? 0 : offset[j];
         w.cnt = size[j];
         w.crpt = crpt; w.ccol = ccol; w.cval = cval;
-        w.lanes = h->cfg.lanes_per_brow;
+        w.lanes = phase ? h->cfg.num_lanes_per_brow : h->cfg.lanes_per_brow;
+        w.unroll = h->cfg.bitmap_unroll;
         w.err = d_err(h);
         const KernelDesc &d = phase ? num_kernel(kid[j]) : sym_kernel(kid[j]);
         size_t smem = 0;
@@ -398,6 +427,7 @@ int spgemm_create(spgemm_handle **out, const spgemm_config *cfg, spgemm_alloc_fn
             h->cfg = *cfg;
         } else {
             default_config(h->cfg);
+            h->cfg_auto = true;
         }
     } while (0);
     if (rc != SPGEMM_OK) {
@@ -413,10 +443,12 @@ int spgemm_set_config(spgemm_handle *h, const spgemm_config *cfg) {
     if (!h) return SPGEMM_ERR_INVALID;
     if (!cfg) {
         default_config(h->cfg);
+        h->cfg_auto = true;
         return SPGEMM_OK;
     }
     if (validate_config(*cfg) != SPGEMM_OK) return SPGEMM_ERR_INVALID;
     h->cfg = *cfg;
+    h->cfg_auto = false;
     return SPGEMM_OK;
 }
 
@@ -441,6 +473,7 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     }
     const int64_t mw = row_end - row_begin;
     h->mw = mw;
+    if (h->cfg_auto) auto_cut(h->cfg, B->cols);
     if ((rc = ensure_arena(h, mw))) return rc;
     int64_t *crpt = static_cast<int64_t *>(dev_alloc(h, sizeof(int64_t) * (size_t)(mw + 1)));
     if (!crpt) return SPGEMM_ERR_OOM;

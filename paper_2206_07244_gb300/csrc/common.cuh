@@ -70,6 +70,22 @@ __device__ __forceinline__ int pick_lanes(int fixed, int64_t nprod, int64_t nnza
     return s;
 }
 
+// Threads per B row for the numeric phase: the smallest power of two that
+// covers the mean referenced B-row length (capped at the row group or a
+// warp), so one round of a sub-group holds the columns of one B row, which
+// are distinct. Taking several overlapping B rows at once (stencil rows)
+// sends lanes to the same table slot in the same round, and float64
+// atomics on one address serialise.
+__device__ __forceinline__ int pick_lanes_distinct(int fixed, int64_t nprod, int64_t nnza, int group) {
+    int cap = group < 32 ? group : 32;
+    if (fixed > 0) return fixed < cap ? fixed : cap;
+    if (nnza <= 0) return 1;
+    int64_t mean = (nprod + nnza - 1) / nnza;
+    int s = 1;
+    while (s < mean && s < cap) s <<= 1;
+    return s;
+}
+
 // --- row-group synchronisation and reductions --------------------------------
 // A row group is TPR consecutive threads. TPR <= 32: a slice of one warp;
 // TPR > 32: the whole block (one row per block).
@@ -218,13 +234,13 @@ __device__ __forceinline__ long long block_excl_scan_ll(long long x, long long &
 // call it (it synchronises the block). A lane's products of one piece (at
 // most kPieceIters) are loaded together before any of them is used, so each
 // thread keeps several L2 loads in flight.
-template <int BLOCK, bool NEED_VAL, typename F>
+template <int BLOCK, bool NEED_VAL, int ITERS = kPieceIters, typename F>
 __device__ __forceinline__ void block_row_walk(const Operands &op, int64_t p0, int64_t p1, int S,
                                                WalkScratch *sc, F &&f) {
     static_assert(BLOCK >= 32 && BLOCK % 32 == 0, "block walk needs whole warps");
     constexpr int CH = BLOCK < kWalkChunk ? BLOCK : kWalkChunk;
     const int nsub = BLOCK / S, sub = threadIdx.x / S, ls = threadIdx.x % S;
-    const long long W = static_cast<long long>(S) * kPieceIters;
+    const long long W = static_cast<long long>(S) * ITERS;
     for (int64_t c = p0; c < p1; c += CH) {
         const int cnt = static_cast<int>(p1 - c < CH ? p1 - c : CH);
         long long pieces = 0;
@@ -242,29 +258,42 @@ __device__ __forceinline__ void block_row_walk(const Operands &op, int64_t p0, i
         }
         long long total;
         const long long ex = block_excl_scan_ll<BLOCK>(pieces, total, sc->warp_tot);
-        if (threadIdx.x < CH) sc->pstart[threadIdx.x] = ex;
+        if (threadIdx.x < CH) sc->pstart[threadIdx.x] = ex;   // entries >= cnt hold `total`
         if (threadIdx.x == 0) sc->pstart[CH] = total;
         __syncthreads();
-        for (long long it = sub; it < total; it += nsub) {
-            int lo = 0, hi = cnt;  // last e with pstart[e] <= it
+        // sub-group `sub` takes a contiguous range of pieces: one binary
+        // search finds its first entry, later entries follow by stepping
+        const long long per = (total + nsub - 1) / nsub;
+        const long long it0 = per * sub;
+        const long long it1 = it0 + per < total ? it0 + per : total;
+        int lo = 0;
+        if (it0 < it1) {
+            int hi = cnt;  // last e with pstart[e] <= it0
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
-                if (sc->pstart[mid] <= it) lo = mid; else hi = mid;
+                if (sc->pstart[mid] <= it0) lo = mid; else hi = mid;
+            }
+        }
+        long long next = sc->pstart[lo + 1];
+        for (long long it = it0; it < it1; ++it) {
+            while (it >= next) {   // skips entries with empty B rows
+                ++lo;
+                next = sc->pstart[lo + 1];
             }
             const long long piece = it - sc->pstart[lo];
             const long long qb = sc->q0[lo] + piece * W + ls;
             const long long qe0 = sc->q0[lo] + sc->len[lo];
             const double a = NEED_VAL ? sc->a[lo] : 0.0;
-            int key[kPieceIters];
-            double bv[kPieceIters];
+            int key[ITERS];
+            double bv[ITERS];
 #pragma unroll
-            for (int u = 0; u < kPieceIters; ++u) {
+            for (int u = 0; u < ITERS; ++u) {
                 const long long q = qb + static_cast<long long>(u) * S;
                 key[u] = q < qe0 ? __ldg(op.bcol + q) : -1;
                 bv[u] = (NEED_VAL && q < qe0) ? __ldg(op.bval + q) : 0.0;
             }
 #pragma unroll
-            for (int u = 0; u < kPieceIters; ++u)
+            for (int u = 0; u < ITERS; ++u)
                 if (key[u] >= 0) f(key[u], a, bv[u]);
         }
         __syncthreads();

@@ -26,6 +26,7 @@ struct BinWork {
     int32_t *ccol;        // numeric only
     double *cval;         // numeric only
     int lanes;            // threads per B row, 0 = per-row automatic
+    int unroll;           // bitmap kernels: products in flight per lane (4 or 8; 0 = 4)
     int *err;             // device error word
 };
 

@@ -139,6 +139,7 @@ extern "C" int spgemm_rowptr_noalloc(const spgemm_csr_in *A, const spgemm_csr_in
         w.cnt = size[j];
         w.crpt = crpt; w.ccol = nullptr; w.cval = nullptr;
         w.lanes = 0;
+        w.unroll = 0;
         w.err = err;
         size_t smem = 0;
         if (sym_kernel(kid[j]).bitmap) {

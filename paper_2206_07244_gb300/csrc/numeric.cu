@@ -47,25 +47,21 @@ __device__ __forceinline__ void num_insert(int *tk, double *tv, int key, double 
 template <int TPR>
 __device__ __forceinline__ int numeric_lanes(const Operands &op, int fixed, int64_t p0,
                                              int64_t p1, int lg, long long *red) {
-    if (fixed > 0) return pick_lanes(fixed, 0, 1, TPR);
+    if (fixed > 0) return pick_lanes_distinct(fixed, 0, 1, TPR);
     long long sum = 0;
     for (int64_t p = p0 + lg; p < p1; p += TPR) {
         const int k = __ldg(op.acol + p);
         sum += ld_rpt(op.brpt, op.b64, k + 1) - ld_rpt(op.brpt, op.b64, k);
     }
     sum = group_sum<TPR>(sum, red);
-    return pick_lanes(0, sum, p1 - p0, TPR);
+    return pick_lanes_distinct(0, sum, p1 - p0, TPR);
 }
 
 // Minimum resident blocks: enough for 2048 threads per SM (<= 32 registers
 // per thread, Sec. 5.6) unless the table is so large that one block fills
-// the SM's shared memory anyway. Sub-warp row groups keep four products in
-// flight per lane (values included), which needs up to 40 registers: they
-// take 1536 threads per SM instead of spilling.
+// the SM's shared memory anyway.
 template <int TPR, int BLOCK, int T>
-__global__ void __launch_bounds__(BLOCK, (T * 12 * (BLOCK / TPR) > 110 * 1024)
-                                             ? 1
-                                             : (TPR <= 32 ? 1536 / BLOCK : 2048 / BLOCK))
+__global__ void __launch_bounds__(BLOCK, (T * 12 * (BLOCK / TPR) > 110 * 1024) ? 1 : 2048 / BLOCK)
 num_hash_kernel(Operands op, BinWork w) {
     constexpr int RPB = BLOCK / TPR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -165,9 +161,8 @@ num_hash_kernel(Operands op, BinWork w) {
     }
 }
 
-constexpr int kBmBlock = 1024;
-
-// Exclusive scan of one unsigned per thread over a 1024-thread block.
+// Exclusive scan of one unsigned per thread over a block of BLOCK threads.
+template <int BLOCK>
 __device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned &total, unsigned *sw) {
     const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
     unsigned inc = x;
@@ -179,13 +174,13 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned &total,
     if (lane == 31) sw[w] = inc;
     __syncthreads();
     if (w == 0) {
-        const unsigned t = sw[lane];
+        const unsigned t = lane < (BLOCK >> 5) ? sw[lane] : 0u;
         unsigned ti = t;
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned y = __shfl_up_sync(0xffffffffu, ti, o);
             if (lane >= static_cast<unsigned>(o)) ti += y;
         }
-        sw[lane] = ti - t;
+        if (lane < (BLOCK >> 5)) sw[lane] = ti - t;
         if (lane == 31) sw[32] = ti;
     }
     __syncthreads();
@@ -193,8 +188,10 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned &total,
     return sw[w] + inc - x;
 }
 
-__global__ void __launch_bounds__(kBmBlock, 1)
+template <int BLOCK, int ITERS>
+__global__ void __launch_bounds__(BLOCK, BLOCK == 1024 ? 1 : 1536 / BLOCK)
 num_bitmap_kernel(Operands op, BinWork w, int words) {
+    constexpr int kBmBlock = BLOCK;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WalkScratch *sc = reinterpret_cast<WalkScratch *>(smem_raw);
     unsigned long long *bm = reinterpret_cast<unsigned long long *>(smem_raw + sizeof(WalkScratch));
@@ -220,9 +217,11 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
         // pass 1: the row's columns inside this window. 32-bit atomics on the
         // two halves of a 64-bit word: shared 64-bit atomics run several
         // times slower on this GPU
-        block_row_walk<kBmBlock, false>(op, p0, p1, S, sc, [&](int key, double, double) {
-            const int64_t rel = static_cast<int64_t>(key) - c0;
-            if (rel >= 0 && rel < span) atomicOr(bm32 + (rel >> 5), 1u << (rel & 31));
+        const int c0i = static_cast<int>(c0);
+        const unsigned span32 = static_cast<unsigned>(span);
+        block_row_walk<kBmBlock, false, ITERS>(op, p0, p1, S, sc, [&](int key, double, double) {
+            const unsigned rel = static_cast<unsigned>(key - c0i);   // one compare covers both ends
+            if (rel < span32) atomicOr(bm32 + (rel >> 5), 1u << (rel & 31));
         });
         // per-word prefix counts = rank of a word's first column in the
         // window; thread t owns a contiguous run of words, so one block scan
@@ -235,7 +234,7 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
             unsigned c = 0;
             for (int i = i0; i < i1; ++i) c += static_cast<unsigned>(__popcll(bm[i]));
             unsigned tot;
-            unsigned ex = block_excl_scan(c, tot, sw);
+            unsigned ex = block_excl_scan<kBmBlock>(c, tot, sw);
             for (int i = i0; i < i1; ++i) {
                 pre[i] = ex;
                 ex += static_cast<unsigned>(__popcll(bm[i]));
@@ -261,13 +260,14 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
             for (int64_t t = threadIdx.x; t < cnt; t += kBmBlock) cval[t] = 0.0;
             __syncthreads();
             // pass 2: each product lands on its column's rank
-            block_row_walk<kBmBlock, true>(op, p0, p1, S, sc, [&](int key, double a, double b) {
-                const int64_t rel = static_cast<int64_t>(key) - c0;
-                if (rel >= 0 && rel < span) {
-                    const int wi = static_cast<int>(rel >> 6);
-                    const int bi = static_cast<int>(rel & 63);
+            block_row_walk<kBmBlock, true, ITERS>(op, p0, p1, S, sc, [&](int key, double a, double b) {
+                const unsigned rel = static_cast<unsigned>(key - c0i);
+                if (rel < span32) {
+                    const unsigned wi = rel >> 6, bi = rel & 63u;
+                    // the column's own bit is set: bits 0..bi shifted to the
+                    // top, counted, minus itself = columns before it in the word
                     const unsigned rank = pre[wi] +
-                        static_cast<unsigned>(__popcll(bm[wi] & ((1ull << bi) - 1ull)));
+                        static_cast<unsigned>(__popcll(bm[wi] << (63u - bi))) - 1u;
                     atomicAdd(cval + rank, a * b);
                 }
             });
@@ -313,7 +313,15 @@ constexpr long long pow2_floor(long long t) {
 
 static NumEntry g_num[] = {NUM_TABLE(NUM_ENTRY)};
 static constexpr int kNumHash = sizeof(g_num) / sizeof(g_num[0]);
-static KernelDesc g_num_bitmap{kBmBlock, kBmBlock, 0, LLONG_MAX, 1, 0};
+static KernelDesc g_num_bitmap{1024, 1024, 0, LLONG_MAX, 1, 0};
+
+using BmFn = void (*)(Operands, BinWork, int);
+// bitmap kernel variants: (threads per block, products in flight per lane)
+static const struct { int block, iters; BmFn fn; } g_num_bm[] = {
+    {1024, 4, &num_bitmap_kernel<1024, 4>}, {1024, 8, &num_bitmap_kernel<1024, 8>},
+    {512, 4, &num_bitmap_kernel<512, 4>},   {256, 4, &num_bitmap_kernel<256, 4>},
+};
+static int g_smem_optin = 0;
 
 int num_kernel_count() { return kNumHash + 1; }
 
@@ -331,8 +339,30 @@ cudaError_t num_prepare(int smem_optin) {
         if (e != cudaSuccess) return e;
     }
     g_num_bitmap.table = static_cast<long long>((smem_optin - sizeof(WalkScratch)) / 12) * 64;
-    return cudaFuncSetAttribute(reinterpret_cast<const void *>(&num_bitmap_kernel),
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+    g_smem_optin = smem_optin;
+    for (const auto &v : g_num_bm) {
+        cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(v.fn),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Bitmap kernel launch shape: the block size that keeps about 2048 threads
+// per SM given how many blocks fit in shared memory (one 1024-thread block
+// when a block needs most of the SM's 228 KB, as for a million columns;
+// 256-thread blocks when the bitmap is small), and `iters` products in
+// flight per lane (4 or 8; 0 = 4).
+static int pick_bitmap_variant(size_t smem_total, int iters) {
+    const size_t per_sm = 228 * 1024;
+    const int fit = static_cast<int>(per_sm / (smem_total + 1024));
+    int block = 1024;
+    if (fit >= 8) block = 256;
+    else if (fit >= 4) block = 512;
+    if (iters == 8) block = 1024;
+    for (int i = 0; i < static_cast<int>(sizeof(g_num_bm) / sizeof(g_num_bm[0])); ++i)
+        if (g_num_bm[i].block == block && g_num_bm[i].iters == (iters == 8 ? 8 : 4)) return i;
+    return 0;
 }
 
 cudaError_t launch_num(int id, const Operands &op, const BinWork &w, size_t smem_bitmap,
@@ -345,8 +375,9 @@ cudaError_t launch_num(int id, const Operands &op, const BinWork &w, size_t smem
         g_num[id].fn<<<static_cast<unsigned>(grid), d.block, d.smem, s>>>(op, w);
     } else {
         const int words = static_cast<int>(smem_bitmap / 12);
-        num_bitmap_kernel<<<static_cast<unsigned>(w.cnt), kBmBlock, smem_bitmap + sizeof(WalkScratch), s>>>(
-            op, w, words);
+        const size_t smem = smem_bitmap + sizeof(WalkScratch);
+        const auto &v = g_num_bm[pick_bitmap_variant(smem, w.unroll)];
+        v.fn<<<static_cast<unsigned>(w.cnt), v.block, smem, s>>>(op, w, words);
     }
     return cudaGetLastError();
 }

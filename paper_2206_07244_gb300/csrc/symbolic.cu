@@ -88,10 +88,10 @@ sym_hash_kernel(Operands op, BinWork w) {
     if (valid && lg == 0) w.crpt[row] = cnt;
 }
 
-constexpr int kBmBlock = 1024;
-
-__global__ void __launch_bounds__(kBmBlock, 1)
+template <int BLOCK, int ITERS>
+__global__ void __launch_bounds__(BLOCK, BLOCK == 1024 ? 1 : 1536 / BLOCK)
 sym_bitmap_kernel(Operands op, BinWork w, int words) {
+    constexpr int kBmBlock = BLOCK;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WalkScratch *sc = reinterpret_cast<WalkScratch *>(smem_raw);
     unsigned *bm = reinterpret_cast<unsigned *>(smem_raw + sizeof(WalkScratch));
@@ -108,9 +108,11 @@ sym_bitmap_kernel(Operands op, BinWork w, int words) {
         const int nw = static_cast<int>(((op.ncols - c0 < span ? op.ncols - c0 : span) + 31) / 32);
         for (int i = threadIdx.x; i < nw; i += kBmBlock) bm[i] = 0u;
         __syncthreads();
-        block_row_walk<kBmBlock, false>(op, p0, p1, S, sc, [&](int key, double, double) {
-            const int64_t rel = static_cast<int64_t>(key) - c0;
-            if (rel >= 0 && rel < span) atomicOr(bm + (rel >> 5), 1u << (rel & 31));
+        const int c0i = static_cast<int>(c0);
+        const unsigned span32 = static_cast<unsigned>(span);
+        block_row_walk<kBmBlock, false, ITERS>(op, p0, p1, S, sc, [&](int key, double, double) {
+            const unsigned rel = static_cast<unsigned>(key - c0i);   // one compare covers both ends
+            if (rel < span32) atomicOr(bm + (rel >> 5), 1u << (rel & 31));
         });
         for (int i = threadIdx.x; i < nw; i += kBmBlock) total += __popc(bm[i]);
         __syncthreads();
@@ -145,7 +147,14 @@ struct SymEntry {
 
 static SymEntry g_sym[] = {SYM_TABLE(SYM_ENTRY)};
 static constexpr int kSymHash = sizeof(g_sym) / sizeof(g_sym[0]);
-static KernelDesc g_sym_bitmap{kBmBlock, kBmBlock, 0, LLONG_MAX, 1, 0};
+static KernelDesc g_sym_bitmap{1024, 1024, 0, LLONG_MAX, 1, 0};
+
+using BmFn = void (*)(Operands, BinWork, int);
+// bitmap kernel variants: (threads per block, products in flight per lane)
+static const struct { int block, iters; BmFn fn; } g_sym_bm[] = {
+    {1024, 4, &sym_bitmap_kernel<1024, 4>}, {1024, 8, &sym_bitmap_kernel<1024, 8>},
+    {512, 4, &sym_bitmap_kernel<512, 4>},   {256, 4, &sym_bitmap_kernel<256, 4>},
+};
 
 int sym_kernel_count() { return kSymHash + 1; }
 
@@ -163,8 +172,26 @@ cudaError_t sym_prepare(int smem_optin) {
         if (e != cudaSuccess) return e;
     }
     g_sym_bitmap.table = static_cast<long long>((smem_optin - sizeof(WalkScratch)) / 4) * 32;
-    return cudaFuncSetAttribute(reinterpret_cast<const void *>(&sym_bitmap_kernel),
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+    for (const auto &v : g_sym_bm) {
+        cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(v.fn),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Same launch-shape rule as the numeric bitmap kernel: about 2048 threads
+// per SM given how many blocks fit in shared memory.
+static int pick_sym_bitmap_variant(size_t smem_total, int iters) {
+    const size_t per_sm = 228 * 1024;
+    const int fit = static_cast<int>(per_sm / (smem_total + 1024));
+    int block = 1024;
+    if (fit >= 8) block = 256;
+    else if (fit >= 4) block = 512;
+    if (iters == 8) block = 1024;
+    for (int i = 0; i < static_cast<int>(sizeof(g_sym_bm) / sizeof(g_sym_bm[0])); ++i)
+        if (g_sym_bm[i].block == block && g_sym_bm[i].iters == (iters == 8 ? 8 : 4)) return i;
+    return 0;
 }
 
 cudaError_t launch_sym(int id, const Operands &op, const BinWork &w, size_t smem_bitmap,
@@ -177,8 +204,9 @@ cudaError_t launch_sym(int id, const Operands &op, const BinWork &w, size_t smem
         g_sym[id].fn<<<static_cast<unsigned>(grid), d.block, d.smem, s>>>(op, w);
     } else {
         const int words = static_cast<int>(smem_bitmap / 4);
-        sym_bitmap_kernel<<<static_cast<unsigned>(w.cnt), kBmBlock, smem_bitmap + sizeof(WalkScratch), s>>>(
-            op, w, words);
+        const size_t smem = smem_bitmap + sizeof(WalkScratch);
+        const auto &v = g_sym_bm[pick_sym_bitmap_variant(smem, w.unroll)];
+        v.fn<<<static_cast<unsigned>(w.cnt), v.block, smem, s>>>(op, w, words);
     }
     return cudaGetLastError();
 }

@@ -17,7 +17,7 @@ def _space():
     for sr, nr, sc, nc, ln in itertools.product(autotune.SYM_RATIOS, autotune.NUM_RATIOS,
                                                 (nsym - 1, nsym - 4, 0), (nnum - 1, nnum - 5, 0),
                                                 (0, 8)):
-        yield autotune.make_config(sr, nr, sc, nc, ln)
+        yield autotune.make_config(sr, nr, sc, nc, ln, 32 - 3 * ln)
 
 
 def test_every_candidate_is_a_valid_configuration():
