@@ -126,7 +126,9 @@ int spgemm_get_config(const spgemm_handle *h, spgemm_config *cfg);
  * the first numeric binning pass, which yields the total. Allocates the
  * output row pointer (row_end - row_begin + 1 int64) and keeps it in the
  * handle until spgemm_numeric. *nnzC receives the number of entries of the
- * window. A.val/B.val are not read. Synchronises the handle's stream. */
+ * window. In SPGEMM_MODE_PLAIN A.val/B.val are not read (they may be NULL);
+ * in SPGEMM_MODE_LEARNED rows are multiplied during this call and NULL
+ * values give SPGEMM_ERR_INVALID. Synchronises the handle's stream. */
 int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A,
                     const spgemm_csr_in *B, int64_t row_begin, int64_t row_end,
                     int64_t *nnzC);
@@ -206,6 +208,62 @@ int spgemm_last_stats(const spgemm_handle *h, int64_t *out, int n);
  * accepts. Returns SPGEMM_ERR_INVALID past the last kernel. */
 int spgemm_kernel_info(int phase, int id, int32_t *threads_per_row,
                        int32_t *block, int64_t *table, int64_t *max_size);
+
+/* ---- Learned row sizing ---------------------------------------------------
+ * The paper sizes every output row with the exact symbolic phase (Sec. 2.2).
+ * In SPGEMM_MODE_LEARNED a small perceptron predicts each row's n_nz from six
+ * row features; a row predicted to fit a shared-memory hash table is
+ * multiplied once into a table sized from the prediction (the one-phase
+ * method of Sec. 2.2: the row goes to temporary memory and is copied into C
+ * after the scan). A row whose keys do not fit is detected in the kernel
+ * and recomputed by the exact symbolic and numeric kernels, as are rows
+ * past the symbolic hash bins, so C is identical to SPGEMM_MODE_PLAIN.
+ *
+ * Predictor: 6 -> 64 -> 64 -> 1, ReLU, float32, parameters in one flat
+ * vector W1 (6x64 row-major), b1 (64), W2 (64x64 row-major), b2 (64),
+ * w3 (64), b3 (1) (spgemm_mlp_param_count() = 4673 floats). Features of
+ * output row i (of M = A.rows): log1p(nnz of A row i), log1p(n_prod_i),
+ * log1p of the max / mean / min length of the referenced B rows (0 for an
+ * empty A row) and log((i + 1) / M). The output approximates log1p(n_nz);
+ * the predicted size is max(1, ceil(expm1(y) * (1 + margin))). */
+#define SPGEMM_MODE_PLAIN   0
+#define SPGEMM_MODE_LEARNED 1
+
+int spgemm_mlp_param_count(void);
+
+/* Copy the predictor's parameters (host or device pointer, 4673 floats)
+ * into the handle, with the safety margin of the predicted sizes. */
+int spgemm_set_predictor(spgemm_handle *h, const float *theta, float margin);
+
+/* SPGEMM_MODE_PLAIN or SPGEMM_MODE_LEARNED (needs a predictor; not between
+ * spgemm_symbolic and spgemm_numeric: SPGEMM_ERR_STATE). */
+int spgemm_set_mode(spgemm_handle *h, int mode);
+
+/* After a learned-mode spgemm_symbolic: rows multiplied in one phase, rows
+ * mispredicted (recomputed exactly), rows past the hash bins (exact), and
+ * entries of temporary memory used. */
+int spgemm_learned_stats(const spgemm_handle *h, int64_t *out, int n);
+
+/* Features of rows [row_begin, row_end) of C = A * B into X (device,
+ * (row_end - row_begin) x 6 floats, row-major). workspace: device memory of
+ * 16 bytes per row. Ordered on `stream`. */
+int spgemm_features(const spgemm_csr_in *A, const spgemm_csr_in *B, int64_t row_begin,
+                    int64_t row_end, float *X, void *workspace, void *stream);
+
+/* y[i] = predictor(X[i]) for n rows (device pointers). */
+int spgemm_mlp_forward(const float *theta, const float *X, int64_t n, float *y, void *stream);
+
+/* Adds to grad (4673 floats, device) the gradient of
+ * sum over these n samples of (y_i - t_i)^2 / n_total, and that sum to
+ * *loss (device float): call once per part of a mini-batch of n_total
+ * samples after zeroing grad and loss. */
+int spgemm_mlp_train_step(const float *theta, const float *X, const float *t, int64_t n,
+                          int64_t n_total, float *grad, float *loss, void *stream);
+
+/* One Adam step (Kingma & Ba, with bias correction; step counts from 1) on
+ * the 4673 parameters; m and v are the moment buffers (device). */
+int spgemm_mlp_adam(float *theta, const float *grad, float *m, float *v, int step, float lr,
+                    float beta1, float beta2, float eps, void *stream);
 
 const char *spgemm_strerror(int code);
 

@@ -156,7 +156,7 @@ class Handle:
     # -- the two phases -----------------------------------------------------------
     def symbolic(self, A: CSR, B: CSR, row_begin: int = 0, row_end: int | None = None) -> int:
         row_end = A.rows if row_end is None else row_end
-        a, b = _csr_in(A, False), _csr_in(B, False)
+        a, b = _csr_in(A), _csr_in(B)   # values: the learned mode multiplies here
         nnz = ctypes.c_int64()
         _abi.check(self._lib.spgemm_symbolic(self._h, ctypes.byref(a), ctypes.byref(b),
                                              row_begin, row_end, ctypes.byref(nnz)),
@@ -194,6 +194,27 @@ class Handle:
         else:
             col, val = out[0][:nnz], out[1][:nnz]
         return CSR(rows, int(c.cols), rpt, col, val)
+
+    # -- learned sizing ------------------------------------------------------------
+    def set_predictor(self, theta, margin: float = 0.25):
+        """theta: 4673 float32 parameters (torch CUDA tensor or numpy array)."""
+        import numpy as np
+        import torch
+        t = theta if isinstance(theta, torch.Tensor) else torch.as_tensor(np.asarray(theta, np.float32))
+        t = t.to(dtype=torch.float32, device=self._device).contiguous()
+        _abi.check(self._lib.spgemm_set_predictor(self._h, ctypes.c_void_p(t.data_ptr()),
+                                                  ctypes.c_float(margin)), "spgemm_set_predictor")
+        torch.cuda.current_stream().synchronize()
+
+    def set_mode(self, mode: str):
+        m = {"plain": 0, "learned": 1}[mode]
+        _abi.check(self._lib.spgemm_set_mode(self._h, m), "spgemm_set_mode")
+
+    def learned_stats(self) -> dict:
+        arr = (ctypes.c_int64 * 4)()
+        _abi.check(self._lib.spgemm_learned_stats(self._h, arr, 4), "spgemm_learned_stats")
+        return {"one_phase_rows": arr[0], "mispredicted_rows": arr[1], "exact_rows": arr[2],
+                "temp_entries": arr[3]}
 
     # -- diagnostics -------------------------------------------------------------
     def stats(self) -> dict:

@@ -21,7 +21,9 @@ EXPORTS = [
     "spgemm_numeric", "spgemm_multiply", "spgemm_status", "spgemm_free",
     "spgemm_destroy", "spgemm_last_stats", "spgemm_kernel_info", "spgemm_strerror",
     "spgemm_multiply_host", "spgemm_bin_stats", "spgemm_set_timing", "spgemm_kernel_times",
-    "spgemm_rowptr_noalloc",
+    "spgemm_rowptr_noalloc", "spgemm_mlp_param_count", "spgemm_set_predictor", "spgemm_set_mode",
+    "spgemm_learned_stats", "spgemm_features", "spgemm_mlp_forward", "spgemm_mlp_train_step",
+    "spgemm_mlp_adam",
 ]
 
 
@@ -89,6 +91,15 @@ def lib(path: str | None = None):
             "spgemm_bin_stats": [P, ctypes.c_int, ctypes.POINTER(I64), ctypes.c_int],
             "spgemm_set_timing": [P, ctypes.c_int],
             "spgemm_rowptr_noalloc": [P, P, P, P, ctypes.POINTER(I64)],
+            "spgemm_mlp_param_count": [],
+            "spgemm_set_predictor": [P, P, ctypes.c_float],
+            "spgemm_set_mode": [P, ctypes.c_int],
+            "spgemm_learned_stats": [P, ctypes.POINTER(I64), ctypes.c_int],
+            "spgemm_features": [P, P, I64, I64, P, P, P],
+            "spgemm_mlp_forward": [P, P, I64, P, P],
+            "spgemm_mlp_train_step": [P, P, P, I64, I64, P, P, P],
+            "spgemm_mlp_adam": [P, P, P, P, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, ctypes.c_float, P],
             "spgemm_kernel_times": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64),
                                     ctypes.c_int, ctypes.c_int],
         }

@@ -16,6 +16,7 @@
 //   6 cleanup   scratch is kept in the handle for the next call; nothing is
 //               freed between launches (Sec. 5.5).
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -72,6 +73,19 @@ struct spgemm_handle {
     long long num_size[kMaxBins] = {};
     int64_t stats[4 + 2 * SPGEMM_MAX_BINS] = {};
     int64_t bin_stats[2][3 * SPGEMM_MAX_BINS] = {};
+    // learned sizing
+    int mode = 0;                 // SPGEMM_MODE_PLAIN / SPGEMM_MODE_LEARNED
+    float *theta = nullptr;       // predictor parameters (device)
+    float margin = 0.25f;
+    unsigned char *lscratch = nullptr;
+    size_t lscratch_bytes = 0;
+    int32_t *tcol = nullptr;      // temporary one-phase rows of the current call
+    double *tval = nullptr;
+    long long lsize[kMaxBins] = {}, loff[kMaxBins] = {}, ltbase[kMaxBins] = {}, ltcap[kMaxBins] = {};
+    long long ltotal = 0;
+    bool lid = false;
+    int64_t xcount = 0;
+    int64_t lstats[4] = {};       // one-phase rows, mispredicted rows, exact rows, temp entries
     // per-kernel CUDA-event timing (off unless requested)
     // pinned staging for spgemm_multiply_host
     unsigned char *stage = nullptr;
@@ -168,6 +182,45 @@ int32_t *d_bins(spgemm_handle *h) {
 long long *d_tiles(spgemm_handle *h) {
     return reinterpret_cast<long long *>(h->arena + kCountersBytes +
                                          align256(sizeof(int32_t) * (size_t)std::max<int64_t>(h->mw, 1)));
+}
+
+// Learned-sizing scratch per window row: features (6 floats), prediction,
+// binning size, exact-path list, and the feature kernel's n_prod/max/min.
+struct LScratch {
+    float *X;
+    long long *pred;
+    int64_t *lsizes;
+    int32_t *xlist;
+    unsigned char *fws;   // n_prod (8 B) + max (4 B) + min (4 B) per row
+};
+
+LScratch lscratch_layout(spgemm_handle *h, int64_t mw) {
+    const size_t m = (size_t)std::max<int64_t>(mw, 1);
+    unsigned char *p = h->lscratch;
+    LScratch L;
+    L.X = reinterpret_cast<float *>(p);                 p += align256(sizeof(float) * 6 * m);
+    L.pred = reinterpret_cast<long long *>(p);          p += align256(sizeof(long long) * m);
+    L.lsizes = reinterpret_cast<int64_t *>(p);          p += align256(sizeof(int64_t) * m);
+    L.xlist = reinterpret_cast<int32_t *>(p);           p += align256(sizeof(int32_t) * m);
+    L.fws = p;
+    return L;
+}
+
+int ensure_lscratch(spgemm_handle *h, int64_t mw) {
+    const size_t m = (size_t)std::max<int64_t>(mw, 1);
+    const size_t need = align256(24 * m) + 2 * align256(8 * m) + align256(4 * m) + align256(16 * m) + 256;
+    if (h->lscratch && h->lscratch_bytes >= need) return SPGEMM_OK;
+    if (h->lscratch) {
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SPGEMM_ERR_CUDA;
+        dev_free(h, h->lscratch);
+    }
+    h->lscratch = static_cast<unsigned char *>(dev_alloc(h, need));
+    h->lscratch_bytes = h->lscratch ? need : 0;
+    return h->lscratch ? SPGEMM_OK : SPGEMM_ERR_OOM;
+}
+
+unsigned long long *d_xcount(spgemm_handle *h) {
+    return reinterpret_cast<unsigned long long *>(h->arena + 2 * sizeof(Counters) + 8);
 }
 
 bool is_pow2_lanes(int x) { return x == 0 || x == 1 || x == 2 || x == 4 || x == 8 || x == 16 || x == 32; }
@@ -349,6 +402,176 @@ int read_counters(spgemm_handle *h) {
     return err ? SPGEMM_ERR_INTERNAL : SPGEMM_OK;
 }
 
+// --- learned sizing (one-phase rows with an exact fallback) -------------------
+// Symbolic part: features -> MLP -> predicted sizes -> bins by prediction;
+// rows predicted to fit a hash table are multiplied once (one-phase kernels,
+// rows to temporary memory, n_nz to C.rpt); rows past the symbolic hash bins
+// and mispredicted rows go to the exact bitmap kernels. Ends like the plain
+// symbolic phase: C.rpt holds every row's n_nz and the total is known.
+int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_t *crpt,
+                     int64_t *nnz_out) {
+    const int64_t mw = op.mw;
+    int rc = ensure_lscratch(h, mw);
+    if (rc) return rc;
+    const LScratch L = lscratch_layout(h, mw);
+    cudaStream_t s = h->stream;
+    const int nb = h->cfg.num_nbins;
+    const int last = nb - 1;   // the numeric bitmap bin: exact path
+    const int64_t cap = nb >= 2 ? h->cfg.num_range[nb - 2] : 0;
+    long long *fnp = reinterpret_cast<long long *>(L.fws);
+    unsigned *fmx = reinterpret_cast<unsigned *>(L.fws + sizeof(long long) * (size_t)mw);
+    unsigned *fmn = fmx + mw;
+    CK(launch_features(op, mrows, fnp, fmx, fmn, L.X, h->sm_count * 8, s));
+    CK(launch_mlp_forward(h->theta, L.X, mw, nullptr, L.pred, h->margin, cap + 1, s));
+    const int64_t exact_above = h->cfg.sym_nbins >= 2 ? h->cfg.sym_range[h->cfg.sym_nbins - 2] : -1;
+    CK(launch_learned_sizes(crpt, L.pred, mw, exact_above, LLONG_MAX / 4, L.lsizes, s));
+    Ranges rn{};
+    rn.nb = nb;
+    for (int j = 0; j < nb; ++j) rn.r[j] = h->cfg.num_range[j];
+    CK(launch_bin_pass1(L.lsizes, mw, rn, op, d_counters(h, 0), nullptr, s));
+    if ((rc = read_counters(h))) return rc;
+    h->lid = plan_bins(h->h_cnt[0], nb, h->lsize, h->loff);
+    if (!h->lid) CK(launch_bin_pass2(L.lsizes, mw, rn, h->loff, d_counters(h, 0), d_bins(h), s));
+    // the exact list starts with the rows of the bitmap bin
+    const long long cnt_last = h->lsize[last];
+    if (cnt_last > 0) {
+        if (h->lid) CK(launch_iota(L.xlist, mw, s));
+        else CK(cudaMemcpyAsync(L.xlist, d_bins(h) + h->loff[last], sizeof(int32_t) * (size_t)cnt_last,
+                                cudaMemcpyDeviceToDevice, s));
+    }
+    unsigned long long *h_x = reinterpret_cast<unsigned long long *>(
+        reinterpret_cast<unsigned char *>(h->h_cnt) + 2 * sizeof(Counters) + 16);
+    *h_x = static_cast<unsigned long long>(cnt_last);
+    CK(cudaMemcpyAsync(d_xcount(h), h_x, sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
+    // temporary rows: bin j's row r at tbase_j + r * cap_j
+    long long total_t = 0;
+    for (int j = 0; j < last; ++j) {
+        h->ltcap[j] = num_kernel(h->cfg.num_kernel[j]).max_size;
+        h->ltbase[j] = total_t;
+        total_t += h->lsize[j] * h->ltcap[j];
+    }
+    h->tcol = nullptr;
+    h->tval = nullptr;
+    h->ltotal = total_t;
+    if (total_t > 0) {
+        h->tcol = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * (size_t)total_t));
+        h->tval = static_cast<double *>(dev_alloc(h, sizeof(double) * (size_t)total_t));
+        if (!h->tcol || !h->tval) return SPGEMM_ERR_OOM;
+    }
+    // one-phase kernels, largest rows first on the side streams
+    CK(cudaEventRecord(h->ev_fork, s));
+    int used = 0;
+    for (int j = last - 1; j >= 0; --j) {
+        if (h->lsize[j] <= 0) continue;
+        cudaStream_t ss = h->serial ? s : h->side[used % kSide];
+        if (!h->serial && used < kSide) CK(cudaStreamWaitEvent(ss, h->ev_fork, 0));
+        BinWork w{};
+        w.bins = h->lid ? nullptr : d_bins(h);
+        w.off = h->lid ? 0 : h->loff[j];
+        w.cnt = h->lsize[j];
+        w.crpt = crpt;
+        w.lanes = h->cfg.num_lanes_per_brow;
+        w.err = d_err(h);
+        w.tcol = h->tcol; w.tval = h->tval;
+        w.tbase = h->ltbase[j]; w.tcap = h->ltcap[j];
+        w.tlimit = total_t;
+        w.pred = L.pred; w.xlist = L.xlist; w.xcount = d_xcount(h);
+        w.xlimit = mw;
+        const int slot = kSlotNumBin + j;
+        time_begin(h, slot, ss);
+        CK(launch_num_onephase(h->cfg.num_kernel[j], op, w, ss));
+        time_end(h, slot, ss);
+        ++used;
+    }
+    for (int i = 0; !h->serial && i < std::min(used, kSide); ++i) {
+        CK(cudaEventRecord(h->ev_side[i], h->side[i]));
+        CK(cudaStreamWaitEvent(s, h->ev_side[i], 0));
+    }
+    CK(cudaMemcpyAsync(h_x, d_xcount(h), sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h->xcount = static_cast<int64_t>(*h_x);
+    if (h->xcount > mw) return SPGEMM_ERR_INTERNAL;
+    // exact symbolic for the bitmap-bin rows and the mispredicted rows
+    if (h->xcount > 0) {
+        BinWork w{};
+        w.bins = L.xlist; w.off = 0; w.cnt = h->xcount;
+        w.crpt = crpt;
+        w.lanes = h->cfg.lanes_per_brow;
+        w.unroll = h->cfg.bitmap_unroll;
+        w.err = d_err(h);
+        const int64_t budget = h->smem_dyn_max - static_cast<int64_t>(sizeof(WalkScratch));
+        const int64_t words = std::min<int64_t>((op.ncols + 31) / 32, budget / 4);
+        time_begin(h, kSlotSymBin + 15, s);
+        CK(launch_sym(sym_kernel_count() - 1, op, w, static_cast<size_t>(std::max<int64_t>(words, 1)) * 4, s));
+        time_end(h, kSlotSymBin + 15, s);
+    }
+    // total n_nz and the scan's tile sums
+    Ranges all{};
+    all.nb = 1;
+    all.r[0] = -1;
+    time_begin(h, kSlotNumPass1, s);
+    CK(launch_bin_pass1(crpt, mw, all, op, d_counters(h, 1), d_tiles(h), s));
+    time_end(h, kSlotNumPass1, s);
+    if ((rc = read_counters(h))) return rc;
+    *nnz_out = static_cast<int64_t>(h->h_cnt[1].total);
+    h->lstats[0] = 0;
+    for (int j = 0; j < last; ++j) h->lstats[0] += h->lsize[j];
+    h->lstats[1] = h->xcount - cnt_last;
+    h->lstats[0] -= h->lstats[1];
+    h->lstats[2] = cnt_last;
+    h->lstats[3] = total_t;
+    return SPGEMM_OK;
+}
+
+// Numeric part: scan, C allocation, copy of the one-phase rows, exact
+// numeric kernel for the exact list.
+int numeric_learned(spgemm_handle *h, const Operands &op, int64_t *crpt, int32_t **pcol,
+                    double **pval, bool given) {
+    cudaStream_t s = h->stream;
+    const LScratch L = lscratch_layout(h, h->mw);
+    time_begin(h, kSlotScan, s);
+    CK(launch_scan(crpt, h->mw, d_tiles(h), s));
+    time_end(h, kSlotScan, s);
+    if (!given) {
+        *pcol = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * (size_t)h->nnz));
+        *pval = static_cast<double *>(dev_alloc(h, sizeof(double) * (size_t)h->nnz));
+        if (!*pcol || !*pval) return SPGEMM_ERR_OOM;
+    }
+    const int last = h->cfg.num_nbins - 1;
+    for (int j = 0; j < last; ++j) {
+        if (h->lsize[j] <= 0) continue;
+        BinWork w{};
+        w.bins = h->lid ? nullptr : d_bins(h);
+        w.off = h->lid ? 0 : h->loff[j];
+        w.cnt = h->lsize[j];
+        w.crpt = crpt; w.ccol = *pcol; w.cval = *pval;
+        w.tcol = h->tcol; w.tval = h->tval;
+        w.tbase = h->ltbase[j]; w.tcap = h->ltcap[j];
+        w.tlimit = h->ltotal;
+        w.pred = L.pred;
+        w.err = d_err(h);
+        CK(launch_copy_rows(w, s));
+    }
+    if (h->xcount > 0) {
+        BinWork w{};
+        w.bins = L.xlist; w.off = 0; w.cnt = h->xcount;
+        w.crpt = crpt; w.ccol = *pcol; w.cval = *pval;
+        w.lanes = h->cfg.num_lanes_per_brow;
+        w.unroll = h->cfg.bitmap_unroll;
+        w.err = d_err(h);
+        const int64_t budget = h->smem_dyn_max - static_cast<int64_t>(sizeof(WalkScratch));
+        const int64_t words = std::min<int64_t>((op.ncols + 63) / 64, budget / 12);
+        time_begin(h, kSlotNumBin + 15, s);
+        CK(launch_num(num_kernel_count() - 1, op, w, static_cast<size_t>(std::max<int64_t>(words, 1)) * 12, s));
+        time_end(h, kSlotNumBin + 15, s);
+    }
+    dev_free(h, h->tcol);
+    dev_free(h, h->tval);
+    h->tcol = nullptr;
+    h->tval = nullptr;
+    return SPGEMM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -468,7 +691,11 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     if (row_begin < 0 || row_end < row_begin || row_end > A->rows) return SPGEMM_ERR_INVALID;
     if (h->state == 1) {  // an earlier symbolic result was never consumed
         dev_free(h, h->crpt);
+        dev_free(h, h->tcol);
+        dev_free(h, h->tval);
         h->crpt = nullptr;
+        h->tcol = nullptr;
+        h->tval = nullptr;
         h->state = 0;
     }
     const int64_t mw = row_end - row_begin;
@@ -490,6 +717,29 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     time_begin(h, kSlotNprod, h->stream);
     if (launch_nprod(op, crpt, h->sm_count * 8, h->stream) != cudaSuccess) return fail(SPGEMM_ERR_CUDA);
     time_end(h, kSlotNprod, h->stream);
+    if (h->mode == SPGEMM_MODE_LEARNED) {
+        // the one-phase kernels multiply during this call: they read values
+        if ((A->nnz > 0 && !A->val) || (B->nnz > 0 && !B->val)) return fail(SPGEMM_ERR_INVALID);
+        int64_t nnz = 0;
+        if ((rc = symbolic_learned(h, op, A->rows, crpt, &nnz))) {
+            dev_free(h, h->tcol);
+            dev_free(h, h->tval);
+            h->tcol = nullptr;
+            h->tval = nullptr;
+            return fail(rc);
+        }
+        h->stats[0] = 0;
+        h->stats[1] = 0;
+        h->stats[2] = nnz;
+        h->stats[3] = static_cast<int64_t>(h->h_cnt[1].max_size);
+        h->crpt = crpt;
+        h->row0 = row_begin;
+        h->ncols = B->cols;
+        h->nnz = nnz;
+        h->state = 1;
+        *nnzC = nnz;
+        return SPGEMM_OK;
+    }
     // step 2: symbolic binning by n_prod
     Ranges rs{};
     rs.nb = h->cfg.sym_nbins;
@@ -551,6 +801,26 @@ int spgemm_numeric(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in
     int64_t *crpt = h->crpt;
     h->crpt = nullptr;
     const Operands op = make_operands(A, B, h->row0, h->mw);
+    if (h->mode == SPGEMM_MODE_LEARNED) {
+        int32_t *ccol = C->col;
+        double *cval = C->val;
+        rc = numeric_learned(h, op, crpt, &ccol, &cval, given);
+        if (rc) {
+            dev_free(h, crpt);
+            if (!given) {
+                dev_free(h, ccol);
+                dev_free(h, cval);
+            }
+            dev_free(h, h->tcol);
+            dev_free(h, h->tval);
+            h->tcol = nullptr;
+            h->tval = nullptr;
+            return rc;
+        }
+        C->rows = h->mw; C->cols = h->ncols; C->nnz = h->nnz;
+        C->rpt = crpt; C->col = ccol; C->val = cval;
+        return SPGEMM_OK;
+    }
     const int nb = h->cfg.num_nbins;
     long long off[kMaxBins] = {};
     long long acc = 0;
@@ -850,10 +1120,40 @@ int spgemm_kernel_times(spgemm_handle *h, double *ms, int64_t *launches, int n, 
     return SPGEMM_OK;
 }
 
+int spgemm_set_predictor(spgemm_handle *h, const float *theta, float margin) {
+    if (!h || !theta || !(margin >= 0.f)) return SPGEMM_ERR_INVALID;
+    if (!h->theta) {
+        h->theta = static_cast<float *>(dev_alloc(h, sizeof(float) * (size_t)mlp_param_count()));
+        if (!h->theta) return SPGEMM_ERR_OOM;
+    }
+    CK(cudaMemcpyAsync(h->theta, theta, sizeof(float) * (size_t)mlp_param_count(), cudaMemcpyDefault,
+                       h->stream));
+    h->margin = margin;
+    return SPGEMM_OK;
+}
+
+int spgemm_set_mode(spgemm_handle *h, int mode) {
+    if (!h || (mode != SPGEMM_MODE_PLAIN && mode != SPGEMM_MODE_LEARNED)) return SPGEMM_ERR_INVALID;
+    if (mode == SPGEMM_MODE_LEARNED && !h->theta) return SPGEMM_ERR_STATE;
+    if (h->state == 1) return SPGEMM_ERR_STATE;
+    h->mode = mode;
+    return SPGEMM_OK;
+}
+
+int spgemm_learned_stats(const spgemm_handle *h, int64_t *out, int n) {
+    if (!h || !out || n < 0) return SPGEMM_ERR_INVALID;
+    for (int i = 0; i < std::min(n, 4); ++i) out[i] = h->lstats[i];
+    return SPGEMM_OK;
+}
+
 int spgemm_destroy(spgemm_handle *h) {
     if (!h) return SPGEMM_OK;
     if (h->side[0]) cudaStreamSynchronize(h->stream);
     if (h->state == 1) dev_free(h, h->crpt);
+    dev_free(h, h->tcol);
+    dev_free(h, h->tval);
+    dev_free(h, h->theta);
+    dev_free(h, h->lscratch);
     dev_free(h, h->arena);
     if (h->side[0]) cudaStreamSynchronize(h->stream);
     for (int i = 0; i < kSide; ++i) {

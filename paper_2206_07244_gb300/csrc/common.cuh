@@ -14,6 +14,7 @@ enum : int {
     DERR_TABLE_FULL = 1,      // a hash probe visited every slot
     DERR_COUNT_MISMATCH = 2,  // numeric row size differs from the symbolic count
     DERR_WINDOW = 3,          // bitmap window bookkeeping failed
+    DERR_BOUNDS = 4,          // a learned-sizing index left its buffer (access skipped)
 };
 
 __device__ __forceinline__ void set_error(int *err, int code) {

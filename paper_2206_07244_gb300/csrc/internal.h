@@ -28,6 +28,15 @@ struct BinWork {
     int lanes;            // threads per B row, 0 = per-row automatic
     int unroll;           // bitmap kernels: products in flight per lane (4 or 8; 0 = 4)
     int *err;             // device error word
+    // one-phase (learned sizing) numeric kernels only
+    int32_t *tcol;        // temporary rows: bin-local row r of this bin at
+    double *tval;         //   tcol/tval + tbase + r * tcap
+    long long tbase, tcap;
+    long long tlimit;     // entries of tcol/tval (bounds check)
+    long long *pred;      // predicted sizes; set to -1 for a row that overflowed
+    int32_t *xlist;       // rows for the exact path (overflowed rows are appended)
+    unsigned long long *xcount;
+    long long xlimit;     // entries of xlist (bounds check)
 };
 
 struct Ranges {
@@ -67,6 +76,7 @@ cudaError_t launch_bin_pass2(const int64_t *sizes, int64_t n, const Ranges &rg,
 // writes crpt[n] = total. tile_sums needs room for ntiles + 1 entries.
 cudaError_t launch_scan(int64_t *crpt, int64_t n, long long *tile_sums, cudaStream_t s);
 int64_t bin_tile_rows();
+cudaError_t launch_iota(int32_t *out, int64_t n, cudaStream_t s);
 
 // --- symbolic.cu / numeric.cu -------------------------------------------------
 int sym_kernel_count();
@@ -79,5 +89,24 @@ cudaError_t launch_sym(int id, const Operands &op, const BinWork &w, size_t smem
                        cudaStream_t s);
 cudaError_t launch_num(int id, const Operands &op, const BinWork &w, size_t smem_bitmap,
                        cudaStream_t s);
+// one-phase numeric kernel `id` (a hash kernel of the numeric table)
+cudaError_t launch_num_onephase(int id, const Operands &op, const BinWork &w, cudaStream_t s);
+
+// --- learned.cu ----------------------------------------------------------------
+int mlp_param_count();
+cudaError_t launch_features(const Operands &op, int64_t mrows, long long *nprod, unsigned *maxlen,
+                            unsigned *minlen, float *X, int grid, cudaStream_t s);
+cudaError_t launch_mlp_forward(const float *theta, const float *X, int64_t n, float *y,
+                               long long *sizes, float margin, long long cap, cudaStream_t s);
+cudaError_t launch_mlp_train(const float *theta, const float *X, const float *t, int64_t n,
+                             int64_t n_total, float *grad, float *loss, cudaStream_t s);
+cudaError_t launch_adam(float *theta, const float *grad, float *m, float *v, int n, int step,
+                        float lr, float b1, float b2, float eps, cudaStream_t s);
+// sizes[i] = min(pred[i], n_prod[i]), or `huge` when n_prod[i] > exact_above
+cudaError_t launch_learned_sizes(const int64_t *nprod, const long long *pred, int64_t n,
+                                 long long exact_above, long long huge, int64_t *sizes,
+                                 cudaStream_t s);
+// copy one-phase rows from temporary memory into C (rows whose pred is -1 skipped)
+cudaError_t launch_copy_rows(const BinWork &w, cudaStream_t s);
 
 }  // namespace ops

@@ -27,18 +27,19 @@
 
 namespace ops {
 
+// Returns false when every slot holds another key (the table is full).
 template <int T>
-__device__ __forceinline__ void num_insert(int *tk, double *tv, int key, double v, int *err) {
+__device__ __forceinline__ bool num_insert(int *tk, double *tv, int key, double v) {
     uint32_t h = hash_slot<T>(key);
     for (int it = 0; it < T; ++it) {
         const int old = atomicCAS(tk + h, -1, key);
         if (old == -1 || old == key) {
             atomicAdd(tv + h, v);
-            return;
+            return true;
         }
         h = next_slot<T>(h);
     }
-    set_error(err, DERR_TABLE_FULL);
+    return false;
 }
 
 // Mean referenced B-row length decides how many threads walk one B row; the
@@ -60,7 +61,12 @@ __device__ __forceinline__ int numeric_lanes(const Operands &op, int fixed, int6
 // Minimum resident blocks: enough for 2048 threads per SM (<= 32 registers
 // per thread, Sec. 5.6) unless the table is so large that one block fills
 // the SM's shared memory anyway.
-template <int TPR, int BLOCK, int T>
+// ONE_PHASE (learned sizing): the row's size is not known; the table was
+// chosen from a prediction. A probe that finds no free slot, or more keys
+// than the table can sort in place, marks the row as mispredicted: it is
+// queued for the exact path and nothing is written. Otherwise the row's
+// size goes to C.rpt and its sorted entries to its temporary slot.
+template <int TPR, int BLOCK, int T, bool ONE_PHASE = false>
 __global__ void __launch_bounds__(BLOCK, (T * 12 * (BLOCK / TPR) > 110 * 1024) ? 1 : 2048 / BLOCK)
 num_hash_kernel(Operands op, BinWork w) {
     constexpr int RPB = BLOCK / TPR;
@@ -69,9 +75,12 @@ num_hash_kernel(Operands op, BinWork w) {
     int *keys_all = reinterpret_cast<int *>(vals_all + RPB * T);
     __shared__ long long red64[32];
     __shared__ int red32[33];
+    __shared__ int full[RPB];   // one-phase: a probe found no free slot in this row's table
     const int g = threadIdx.x / TPR, lg = threadIdx.x % TPR;
     int *tk = keys_all + g * T;
     double *tv = vals_all + g * T;
+    bool failed = false;
+    if (lg == 0) full[g] = 0;
     const int64_t r = static_cast<int64_t>(blockIdx.x) * RPB + g;
     const bool valid = r < w.cnt;
     const int64_t row = valid ? (w.bins ? static_cast<int64_t>(w.bins[w.off + r]) : w.off + r) : 0;
@@ -81,8 +90,10 @@ num_hash_kernel(Operands op, BinWork w) {
     }
     int64_t cbase = 0, n_expect = 0, p0 = 0, p1 = 0;
     if (valid) {
-        cbase = w.crpt[row];
-        n_expect = w.crpt[row + 1] - cbase;
+        if (!ONE_PHASE) {
+            cbase = w.crpt[row];
+            n_expect = w.crpt[row + 1] - cbase;
+        }
         const int64_t ar = op.row0 + row;
         p0 = ld_rpt(op.arpt, op.a64, ar);
         p1 = ld_rpt(op.arpt, op.a64, ar + 1);
@@ -94,12 +105,16 @@ num_hash_kernel(Operands op, BinWork w) {
         WalkScratch *sc = reinterpret_cast<WalkScratch *>(
             smem_raw + (sizeof(int) + sizeof(double)) * (size_t)RPB * T);
         block_row_walk<BLOCK, true>(op, p0, p1, S, sc, [&](int key, double a, double b) {
-            num_insert<T>(tk, tv, key, a * b, w.err);
+            if (!num_insert<T>(tk, tv, key, a * b)) failed = true;
         });
     } else {
         group_row_walk<TPR, true>(op, p0, p1, S, [&](int key, double a, double b) {
-            num_insert<T>(tk, tv, key, a * b, w.err);
+            if (!num_insert<T>(tk, tv, key, a * b)) failed = true;
         });
+    }
+    if (failed) {
+        if (ONE_PHASE) full[g] = 1;
+        else set_error(w.err, DERR_TABLE_FULL);
     }
     group_sync<TPR>();
     // condense: occupied slots move to the front, chunk by chunk; a write
@@ -123,12 +138,27 @@ num_hash_kernel(Operands op, BinWork w) {
         n += tot;
         group_sync<TPR>();
     }
-    if (valid && n != n_expect) set_error(w.err, DERR_COUNT_MISMATCH);
     int P = 1;
     while (P < n) P <<= 1;
-    if (P > T) {  // cannot happen within the kernel's capacity; never index past the table
-        set_error(w.err, DERR_TABLE_FULL);
-        P = 1;
+    if constexpr (ONE_PHASE) {
+        // mispredicted: queue the row for the exact path, write nothing else
+        if (full[g] || P > T) {
+            if (valid && lg == 0) {   // C.rpt keeps n_prod for the exact symbolic kernel
+                w.pred[row] = -1;
+                const unsigned long long at = atomicAdd(w.xcount, 1ull);
+                if (at < static_cast<unsigned long long>(w.xlimit)) w.xlist[at] = static_cast<int32_t>(row);
+                else set_error(w.err, DERR_BOUNDS);
+            }
+            return;   // uniform over the row group
+        }
+        n_expect = n;
+        if (valid && lg == 0) w.crpt[row] = n;
+    } else {
+        if (valid && n != n_expect) set_error(w.err, DERR_COUNT_MISMATCH);
+        if (P > T) {  // cannot happen within the kernel's capacity; never index past the table
+            set_error(w.err, DERR_TABLE_FULL);
+            P = 1;
+        }
     }
     for (int s = n + lg; s < P; s += TPR) tk[s] = INT_MAX;
     group_sync<TPR>();
@@ -154,9 +184,18 @@ num_hash_kernel(Operands op, BinWork w) {
     }
     if (valid) {
         const int64_t m = n < n_expect ? n : n_expect;
-        for (int64_t t = lg; t < m; t += TPR) {
-            w.ccol[cbase + t] = tk[t];
-            w.cval[cbase + t] = tv[t];
+        int32_t *ocol = w.ccol + cbase;
+        double *oval = w.cval + cbase;
+        bool in_bounds = true;
+        if (ONE_PHASE) {
+            ocol = w.tcol + w.tbase + r * w.tcap;
+            oval = w.tval + w.tbase + r * w.tcap;
+            in_bounds = m <= w.tcap && w.tbase + r * w.tcap + m <= w.tlimit;
+            if (!in_bounds && lg == 0) set_error(w.err, DERR_BOUNDS);
+        }
+        for (int64_t t = lg; in_bounds && t < m; t += TPR) {
+            ocol[t] = tk[t];
+            oval[t] = tv[t];
         }
     }
 }
@@ -312,6 +351,9 @@ constexpr long long pow2_floor(long long t) {
      &num_hash_kernel<TPR, BLOCK, T>},
 
 static NumEntry g_num[] = {NUM_TABLE(NUM_ENTRY)};
+
+#define NUM_ONEPHASE_ENTRY(TPR, BLOCK, T) &num_hash_kernel<TPR, BLOCK, T, true>,
+static NumFn g_num_onephase[] = {NUM_TABLE(NUM_ONEPHASE_ENTRY)};
 static constexpr int kNumHash = sizeof(g_num) / sizeof(g_num[0]);
 static KernelDesc g_num_bitmap{1024, 1024, 0, LLONG_MAX, 1, 0};
 
@@ -334,6 +376,12 @@ cudaError_t num_prepare(int smem_optin) {
     // shared memory, so a table of exactly 48 KB already needs it.
     for (int i = 0; i < kNumHash; ++i) {
         cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(g_num[i].fn),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(g_num[i].d.smem));
+        if (e != cudaSuccess) return e;
+    }
+    for (int i = 0; i < kNumHash; ++i) {
+        cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(g_num_onephase[i]),
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(g_num[i].d.smem));
         if (e != cudaSuccess) return e;
@@ -363,6 +411,45 @@ static int pick_bitmap_variant(size_t smem_total, int iters) {
     for (int i = 0; i < static_cast<int>(sizeof(g_num_bm) / sizeof(g_num_bm[0])); ++i)
         if (g_num_bm[i].block == block && g_num_bm[i].iters == (iters == 8 ? 8 : 4)) return i;
     return 0;
+}
+
+cudaError_t launch_num_onephase(int id, const Operands &op, const BinWork &w, cudaStream_t s) {
+    if (w.cnt <= 0) return cudaSuccess;
+    if (id < 0 || id >= kNumHash) return cudaErrorInvalidValue;
+    const KernelDesc &d = g_num[id].d;
+    const int rpb = d.block / d.tpr;
+    const int64_t grid = (w.cnt + rpb - 1) / rpb;
+    g_num_onephase[id]<<<static_cast<unsigned>(grid), d.block, d.smem, s>>>(op, w);
+    return cudaGetLastError();
+}
+
+// Copies the one-phase rows of a bin from their temporary slots into C: one
+// warp per row, rows marked -1 in pred (mispredicted) are skipped.
+__global__ void copy_rows_kernel(BinWork w) {
+    const int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= w.cnt) return;
+    const int64_t row = w.bins ? static_cast<int64_t>(w.bins[w.off + r]) : w.off + r;
+    if (w.pred[row] < 0) return;
+    const int64_t base = w.crpt[row];
+    const int64_t n = w.crpt[row + 1] - base;
+    const int32_t *scol = w.tcol + w.tbase + r * w.tcap;
+    const double *sval = w.tval + w.tbase + r * w.tcap;
+    if (n > w.tcap || w.tbase + r * w.tcap + n > w.tlimit) {
+        if (lane == 0) set_error(w.err, DERR_BOUNDS);
+        return;
+    }
+    for (int64_t t = lane; t < n; t += 32) {
+        w.ccol[base + t] = scol[t];
+        w.cval[base + t] = sval[t];
+    }
+}
+
+cudaError_t launch_copy_rows(const BinWork &w, cudaStream_t s) {
+    if (w.cnt <= 0) return cudaSuccess;
+    const int64_t threads = w.cnt * 32;
+    copy_rows_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, s>>>(w);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_num(int id, const Operands &op, const BinWork &w, size_t smem_bitmap,

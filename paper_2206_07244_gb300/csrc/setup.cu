@@ -299,4 +299,15 @@ cudaError_t launch_scan(int64_t *crpt, int64_t n, long long *tile_sums, cudaStre
     return cudaGetLastError();
 }
 
+__global__ void iota_kernel(int32_t *out, int64_t n) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = static_cast<int32_t>(i);
+}
+
+cudaError_t launch_iota(int32_t *out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    iota_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(out, n);
+    return cudaGetLastError();
+}
+
 }  // namespace ops

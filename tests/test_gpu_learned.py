@@ -1,0 +1,183 @@
+"""Learned row sizing on the GPU against the CPU oracle (oracle/mlp.py in
+float64): features, forward pass, gradients, Adam; and the learned-mode
+product, which must equal the oracle's C whatever the predictor says
+(trained, predicting 1 for every row, or predicting more than any table)."""
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.mlp as omlp
+import workloads as W
+from helpers import assert_values_close
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2206_07244_gb300 as ops  # noqa: E402
+from paper_2206_07244_gb300 import learned  # noqa: E402
+
+ops.build()
+
+
+def dev(m):
+    return ops.CSR.from_workload(m)
+
+
+def test_features_match_oracle():
+    for A, B in ((W.rmat(11, 8, seed=3), None), (W.random_csr(300, 200, 0.05, seed=1),
+                                                 W.random_csr(200, 150, 0.1, seed=2))):
+        B = A if B is None else B
+        X = learned.features(dev(A), dev(B)).cpu().numpy().astype(np.float64)
+        Xo = omlp.features(A, B)
+        assert np.allclose(X, Xo, rtol=3e-6, atol=1e-6)
+    # a row window uses the global row index for the last feature
+    A = W.rmat(10, 8, seed=4)
+    X = learned.features(dev(A), dev(A), 100, 300).cpu().numpy()
+    assert np.allclose(X, omlp.features(A, A)[100:300], rtol=3e-6, atol=1e-6)
+
+
+def test_forward_matches_oracle():
+    rng = np.random.default_rng(0)
+    theta = W.mlp_init(seed=1)
+    theta[384:448] = rng.normal(0, 0.1, 64)
+    X = rng.normal(size=(1000, 6))
+    p = learned.Predictor(theta)
+    y = p.forward(torch.as_tensor(X, dtype=torch.float32).cuda()).cpu().numpy()
+    yo, _ = omlp.forward(theta.astype(np.float32).astype(np.float64), X.astype(np.float32).astype(np.float64))
+    assert np.allclose(y, yo, rtol=1e-5, atol=1e-5)
+
+
+def test_gradient_matches_oracle():
+    rng = np.random.default_rng(1)
+    theta = W.mlp_init(seed=2)
+    theta[384:448] = rng.normal(0, 0.1, 64)
+    theta = theta.astype(np.float32).astype(np.float64)
+    X = rng.normal(size=(300, 6)).astype(np.float32).astype(np.float64)   # 3 blocks, ragged
+    t = rng.normal(size=300).astype(np.float32).astype(np.float64)
+    p = learned.Predictor(theta)
+    loss, grad = p.gradient(torch.as_tensor(X, dtype=torch.float32).cuda(),
+                            torch.as_tensor(t, dtype=torch.float32).cuda())
+    Lo, go = omlp.backward(theta, X, t)
+    g = grad.cpu().numpy().astype(np.float64)
+    assert abs(float(loss.item()) - Lo) <= 1e-5 * Lo
+    scale = np.abs(go) + 1e-3 * np.abs(go).max()
+    assert np.all(np.abs(g - go) <= 1e-4 * scale)
+
+
+def test_adam_matches_oracle():
+    rng = np.random.default_rng(3)
+    theta = rng.normal(size=omlp.N_PARAMS).astype(np.float32)
+    p = learned.Predictor(theta)
+    g = rng.normal(size=omlp.N_PARAMS).astype(np.float32)
+    p.grad.copy_(torch.as_tensor(g).cuda())
+    p.adam(lr=0.01)
+    p.grad.copy_(torch.as_tensor(g * 0.5).cuda())
+    p.adam(lr=0.01)
+    th, m, v = theta.astype(np.float64), np.zeros(omlp.N_PARAMS), np.zeros(omlp.N_PARAMS)
+    th, m, v = omlp.adam(th, g.astype(np.float64), m, v, 1, lr=0.01)
+    th, m, v = omlp.adam(th, 0.5 * g.astype(np.float64), m, v, 2, lr=0.01)
+    assert np.allclose(p.theta.cpu().numpy(), th, rtol=1e-5, atol=1e-6)
+
+
+def test_training_reduces_loss():
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(5000, 6))
+    t = 0.5 * X[:, 0] + np.maximum(X[:, 1], 0) + 1.0
+    p = learned.Predictor(seed=0)
+    hist = p.fit(torch.as_tensor(X, dtype=torch.float32).cuda(),
+                 torch.as_tensor(t, dtype=torch.float32).cuda(), epochs=40, batch=1024, lr=3e-3)
+    assert hist[-1] < 0.05 * hist[0]
+
+
+@pytest.fixture(scope="module")
+def trained():
+    pairs = [(dev(m), dev(m)) for m in (W.rmat(11, 8, seed=21), W.rmat(12, 16, seed=22),
+                                       W.banded(4096, 7, seed=23), W.block_diagonal(4096, 64, 12, 24),
+                                       W.stencil27(10, seed=25))]
+    X, t = learned.training_set(pairs, rows_per_matrix=2048, seed=0)
+    p = learned.Predictor(seed=0)
+    hist = p.fit(X, t, epochs=60, batch=1024, lr=3e-3)
+    assert hist[-1] < 0.2 * hist[0]
+    return p
+
+
+def _check_learned(A, theta, margin=0.25):
+    with ops.Handle() as h:
+        h.set_predictor(theta, margin)
+        h.set_mode("learned")
+        C = h.multiply(dev(A), dev(A))
+        h.status()
+        st = h.learned_stats()
+        got = C.numpy()
+    rpt, col, val, ab = oracle.spgemm(A, A)
+    assert np.array_equal(got[0], rpt) and np.array_equal(got[1], col)
+    assert_values_close(got[2], val, ab)
+    return st
+
+
+@pytest.mark.parametrize("case", ["rmat", "stencil", "banded"])
+def test_learned_mode_is_exact_with_trained_predictor(trained, case):
+    A = {"rmat": W.rmat(13, 12, seed=31), "stencil": W.stencil27(14, seed=3),
+         "banded": W.banded(5000, 20, seed=5)}[case]
+    st = _check_learned(A, trained.theta)
+    assert st["one_phase_rows"] > 0
+
+
+def test_learned_mode_underprediction_falls_back():
+    A = W.rmat(12, 16, seed=41)
+    theta = np.zeros(omlp.N_PARAMS, dtype=np.float32)   # y = 0: predicted size 1
+    st = _check_learned(A, theta, margin=0.0)
+    assert st["mispredicted_rows"] > 0
+
+
+def test_learned_mode_overprediction_is_the_nprod_bound():
+    # y = 30 predicts more than any table; the size used is then
+    # min(prediction, n_prod) = n_prod, an upper bound of n_nz, so no row is
+    # mispredicted; rows whose n_prod passes the largest table go exact.
+    A = W.rmat(11, 8, seed=42)
+    theta = np.zeros(omlp.N_PARAMS, dtype=np.float32)
+    theta[-1] = 30.0
+    st = _check_learned(A, theta)
+    assert st["mispredicted_rows"] == 0 and st["exact_rows"] > 0 and st["one_phase_rows"] > 0
+
+
+def test_learned_mode_row_window_and_int64(trained):
+    A = W.rmat(12, 8, seed=43)
+    dA = ops.CSR.from_arrays(A.rows, A.cols, A.rpt.astype(np.int64), A.col, A.val)
+    with ops.Handle() as h:
+        h.set_predictor(trained.theta)
+        h.set_mode("learned")
+        h.symbolic(dA, dA, 1000, 3000)
+        C = h.numeric(dA, dA)
+        h.status()
+        got = C.numpy()
+    rpt, col, val, ab = oracle.spgemm(A, A, 1000, 3000)
+    assert np.array_equal(got[0], rpt) and np.array_equal(got[1], col)
+    assert_values_close(got[2], val, ab)
+
+
+def test_mode_needs_predictor():
+    with ops.Handle() as h:
+        with pytest.raises(ops.SpgemmError):
+            h.set_mode("learned")
+
+
+def test_learned_symbolic_without_values_is_rejected(trained):
+    # In learned mode rows are multiplied during the symbolic call, so it
+    # needs A.val/B.val; without them the call must fail cleanly.
+    import ctypes
+    from paper_2206_07244_gb300 import _abi, _csr_in
+    A = dev(W.rmat(10, 8, seed=44))
+    with ops.Handle() as h:
+        h.set_predictor(trained.theta)
+        h.set_mode("learned")
+        a, b = _csr_in(A, False), _csr_in(A, False)
+        nnz = ctypes.c_int64()
+        rc = _abi.lib().spgemm_symbolic(h._h, ctypes.byref(a), ctypes.byref(b), 0, A.rows,
+                                        ctypes.byref(nnz))
+        assert rc == -1
+        h.status()
