@@ -265,6 +265,42 @@ int spgemm_mlp_train_step(const float *theta, const float *X, const float *t, in
 int spgemm_mlp_adam(float *theta, const float *grad, float *m, float *v, int step, float lr,
                     float beta1, float beta2, float eps, void *stream);
 
+/* ---- Batched products ------------------------------------------------------
+ * Many products C_i = A_i * B_i with small rows (for example the Galerkin
+ * products P^T (A P) of an algebraic-multigrid setup) run in one persistent
+ * kernel, captured once in a CUDA graph. B_i may be the C of an earlier
+ * product j < i (b_from[i] = j; -1 or b_from NULL: B[i] is an input, and
+ * B[i] is then ignored when b_from[i] >= 0). Each product follows the
+ * two-phase method (symbolic row tiles, scan, numeric row tiles); blocks
+ * take work items from a device queue and wait, with a bound, for the items
+ * they depend on. Inputs are device CSR that must stay valid while the
+ * batch exists. The plan (spgemm_batch_create) bounds every row's size by
+ * its number of intermediate products and places every C in one arena; a
+ * batch whose largest row bound exceeds the largest table (256) is
+ * rejected with SPGEMM_ERR_INVALID. */
+typedef struct spgemm_batch spgemm_batch;
+typedef struct {
+    int32_t variant;     /* -1: smallest table that holds the largest row;
+                            0, 1, 2: 8 lanes / 64 slots, 16 / 128, 32 / 256 */
+    int32_t tile_rows;   /* rows per work item (0: 4 per row group)        */
+    int64_t spin_limit;  /* polls of a bounded wait, 200 ns apart (0: 2^22) */
+} spgemm_batch_options;
+
+int spgemm_batch_create(spgemm_batch **b, spgemm_handle *h, int n, const spgemm_csr_in *A,
+                        const spgemm_csr_in *B, const int32_t *b_from,
+                        const spgemm_batch_options *opt);
+/* Enqueue one run (one graph launch) on the handle's stream. */
+int spgemm_batch_run(spgemm_batch *b);
+/* Wait for the last run: SPGEMM_OK, SPGEMM_ERR_TIMEOUT (a bounded wait ran
+ * out) or SPGEMM_ERR_INTERNAL (a row outgrew its bound); reads the sizes. */
+int spgemm_batch_sync(spgemm_batch *b);
+/* Product i of the last synchronised run: device pointers into the batch's
+ * arena (valid until the next run or destroy), C.rpt int64 (rows + 1). */
+int spgemm_batch_result(const spgemm_batch *b, int i, spgemm_csr_out *C);
+/* products, work items, blocks, lanes per row, table slots, rows per item */
+int spgemm_batch_info(const spgemm_batch *b, int64_t *out, int n);
+int spgemm_batch_destroy(spgemm_batch *b);
+
 const char *spgemm_strerror(int code);
 
 /* ---- Sizing C without allocating device memory --------------------------

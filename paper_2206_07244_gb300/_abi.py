@@ -23,7 +23,8 @@ EXPORTS = [
     "spgemm_multiply_host", "spgemm_bin_stats", "spgemm_set_timing", "spgemm_kernel_times",
     "spgemm_rowptr_noalloc", "spgemm_mlp_param_count", "spgemm_set_predictor", "spgemm_set_mode",
     "spgemm_learned_stats", "spgemm_features", "spgemm_mlp_forward", "spgemm_mlp_train_step",
-    "spgemm_mlp_adam",
+    "spgemm_mlp_adam", "spgemm_batch_create", "spgemm_batch_run", "spgemm_batch_sync",
+    "spgemm_batch_result", "spgemm_batch_info", "spgemm_batch_destroy",
 ]
 
 
@@ -42,6 +43,11 @@ class CsrIn(ctypes.Structure):
 class CsrOut(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("rpt", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class BatchOptions(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
+                ("spin_limit", ctypes.c_int64)]
 
 
 class Config(ctypes.Structure):
@@ -92,6 +98,12 @@ def lib(path: str | None = None):
             "spgemm_set_timing": [P, ctypes.c_int],
             "spgemm_rowptr_noalloc": [P, P, P, P, ctypes.POINTER(I64)],
             "spgemm_mlp_param_count": [],
+            "spgemm_batch_create": [ctypes.POINTER(P), P, ctypes.c_int, P, P, P, P],
+            "spgemm_batch_run": [P],
+            "spgemm_batch_sync": [P],
+            "spgemm_batch_result": [P, ctypes.c_int, P],
+            "spgemm_batch_info": [P, ctypes.POINTER(I64), ctypes.c_int],
+            "spgemm_batch_destroy": [P],
             "spgemm_set_predictor": [P, P, ctypes.c_float],
             "spgemm_set_mode": [P, ctypes.c_int],
             "spgemm_learned_stats": [P, ctypes.POINTER(I64), ctypes.c_int],

@@ -115,3 +115,57 @@ def tune(A: CSR, B: CSR, reps: int = 3, log=None) -> tuple[dict, list]:
                 best, params = t, cand
     history = [(json.loads(k), v) for k, v in seen.items()]
     return make_config(**params), history
+
+
+# batch kernel variants (lanes per row, table slots): (8, 64), (16, 128), (32, 256)
+BATCH_VARIANTS = 3
+
+
+def time_batch(b, reps: int = 3, warmup: int = 1) -> float:
+    """Median wall-clock milliseconds of one batch run (graph launch through
+    the synchronising read of the sizes)."""
+    import time
+
+    import torch
+    for _ in range(warmup):
+        b.run()
+        b.sync()
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.run()
+        b.sync()
+        ts.append((time.perf_counter() - t0) * 1e3)
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
+def tune_batch(handle: Handle, As, Bs, b_from, reps: int = 3, log=None) -> tuple[dict, list]:
+    """Threads per row, table size (the kernel variant) and rows per work item
+    of a batch, by exhaustive timing: every variant whose table holds the
+    batch's largest row bound, with 1, 2, 4, 8, 16 or 32 row groups' worth of
+    rows per item. Returns ({"variant", "tile_rows", "ms"}, history)."""
+    from . import SpgemmError
+    from .batch import Batch
+    hist = []
+    best = None
+    for variant in range(BATCH_VARIANTS):
+        try:
+            with Batch(handle, As, Bs, b_from, variant=variant) as b:
+                groups_per_block = 256 // b.info()["lanes_per_row"]
+        except SpgemmError as e:
+            if e.code == -1:     # this table cannot hold the largest row
+                continue
+            raise
+        for mult in (1, 2, 4, 8, 16, 32):
+            tile = groups_per_block * mult
+            with Batch(handle, As, Bs, b_from, variant=variant, tile_rows=tile) as b:
+                ms = time_batch(b, reps)
+            rec = {"variant": variant, "tile_rows": tile, "ms": round(ms, 4)}
+            hist.append(rec)
+            if log:
+                log(rec)
+            if best is None or ms < best["ms"]:
+                best = rec
+    return best, hist

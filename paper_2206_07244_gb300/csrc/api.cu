@@ -17,6 +17,7 @@
 //               freed between launches (Sec. 5.5).
 #include <algorithm>
 #include <climits>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -1170,6 +1171,278 @@ int spgemm_destroy(spgemm_handle *h) {
     if (h->stage_rpt) cudaFreeHost(h->stage_rpt);
     if (h->pool) cudaMemPoolDestroy(h->pool);
     delete h;
+    return SPGEMM_OK;
+}
+
+}  // extern "C"
+
+// --- batched products (one persistent launch under a CUDA graph) ---------------
+struct spgemm_batch {
+    spgemm_handle *h = nullptr;
+    int n = 0;
+    std::vector<BatchProb> probs;
+    std::vector<int64_t> M, N;
+    BatchProb *d_probs = nullptr;
+    BatchItem *d_items = nullptr;
+    int nitems = 0;
+    unsigned char *d_state = nullptr;   // BatchState, then done_s, xflag, done_n
+    size_t state_bytes = 0;
+    unsigned char *arena = nullptr;
+    size_t arena_bytes = 0;
+    int variant = 0, tile_rows = 0, grid = 0;
+    long long spin_limit = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t *d_totals = nullptr;        // gathered C.rpt[M] of every product
+    std::vector<int64_t> nnz;
+    int last_rc = SPGEMM_OK;
+};
+
+namespace {
+
+__global__ void gather_totals_kernel(const BatchProb *probs, int n, int64_t *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = probs[i].crpt[probs[i].M];
+}
+
+void batch_release(spgemm_batch *b) {
+    spgemm_handle *h = b->h;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    dev_free(h, b->d_probs);
+    dev_free(h, b->d_items);
+    dev_free(h, b->d_state);
+    dev_free(h, b->arena);
+    dev_free(h, b->d_totals);
+}
+
+}  // namespace
+
+extern "C" {
+
+int spgemm_batch_create(spgemm_batch **out, spgemm_handle *h, int n, const spgemm_csr_in *A,
+                        const spgemm_csr_in *B, const int32_t *b_from,
+                        const spgemm_batch_options *opt) {
+    if (!out || !h || n < 0 || (n > 0 && (!A || !B))) return SPGEMM_ERR_INVALID;
+    *out = nullptr;
+    spgemm_batch *b = new (std::nothrow) spgemm_batch();
+    if (!b) return SPGEMM_ERR_OOM;
+    b->h = h;
+    b->n = n;
+    b->probs.resize(n);
+    b->M.resize(n);
+    b->N.resize(n);
+    b->nnz.assign(n, 0);
+    int rc = SPGEMM_OK;
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(h->stream);
+        batch_release(b);
+        delete b;
+        return code;
+    };
+    // shapes and dependencies
+    std::vector<int> level(n, 0);
+    for (int i = 0; i < n; ++i) {
+        const int dep = b_from ? b_from[i] : -1;
+        if ((rc = check_csr_in(&A[i]))) return fail(rc);
+        if (dep >= i) return fail(SPGEMM_ERR_INVALID);
+        if (dep < 0) {
+            if ((rc = check_csr_in(&B[i]))) return fail(rc);
+            if (A[i].cols != B[i].rows) return fail(SPGEMM_ERR_SHAPE);
+            if ((A[i].nnz > 0 && !A[i].val) || (B[i].nnz > 0 && !B[i].val)) return fail(SPGEMM_ERR_INVALID);
+            b->N[i] = B[i].cols;
+        } else {
+            if (A[i].cols != b->M[dep]) return fail(SPGEMM_ERR_SHAPE);
+            if (A[i].nnz > 0 && !A[i].val) return fail(SPGEMM_ERR_INVALID);
+            b->N[i] = b->N[dep];
+            level[i] = level[dep] + 1;
+        }
+        b->M[i] = A[i].rows;
+    }
+    // row bounds: exact n_prod for products of input matrices; for a product
+    // whose B is an earlier C, the n_prod of that C's rows bounds their size,
+    // so a pseudo row pointer built from those bounds gives a bound here
+    std::vector<std::vector<int64_t>> bound(n);
+    std::vector<int64_t> cap(n, 0);
+    int64_t maxrow = 0;
+    int64_t *d_b = nullptr, *d_rp = nullptr;
+    size_t d_b_n = 0, d_rp_n = 0;
+    for (int i = 0; i < n; ++i) {
+        const int dep = b_from ? b_from[i] : -1;
+        const int64_t M = b->M[i];
+        if ((size_t)(M + 1) > d_b_n) {
+            dev_free(h, d_b);
+            d_b_n = (size_t)(M + 1);
+            d_b = static_cast<int64_t *>(dev_alloc(h, sizeof(int64_t) * d_b_n));
+            if (!d_b) return fail(SPGEMM_ERR_OOM);
+        }
+        Operands op{};
+        op.arpt = A[i].rpt; op.a64 = A[i].rpt_is_i64 ? 1 : 0; op.acol = A[i].col;
+        op.row0 = 0; op.mw = M; op.ncols = b->N[i];
+        if (dep < 0) {
+            op.brpt = B[i].rpt; op.b64 = B[i].rpt_is_i64 ? 1 : 0;
+        } else {
+            const std::vector<int64_t> &bd = bound[dep];
+            std::vector<int64_t> rp(bd.size() + 1, 0);
+            for (size_t k = 0; k < bd.size(); ++k) rp[k + 1] = rp[k] + bd[k];
+            if (rp.size() > d_rp_n) {
+                dev_free(h, d_rp);
+                d_rp_n = rp.size();
+                d_rp = static_cast<int64_t *>(dev_alloc(h, sizeof(int64_t) * d_rp_n));
+                if (!d_rp) return fail(SPGEMM_ERR_OOM);
+            }
+            CK(cudaMemcpyAsync(d_rp, rp.data(), sizeof(int64_t) * rp.size(), cudaMemcpyHostToDevice, h->stream));
+            op.brpt = d_rp; op.b64 = 1;
+        }
+        CK(cudaMemsetAsync(d_b, 0, sizeof(int64_t) * (size_t)(M + 1), h->stream));
+        CK(launch_nprod(op, d_b, h->sm_count * 4, h->stream));
+        bound[i].resize((size_t)M);
+        if (M > 0)
+            CK(cudaMemcpyAsync(bound[i].data(), d_b, sizeof(int64_t) * (size_t)M, cudaMemcpyDeviceToHost,
+                               h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        for (int64_t v : bound[i]) {
+            cap[i] += v;
+            maxrow = std::max(maxrow, v);
+        }
+    }
+    dev_free(h, d_b);
+    dev_free(h, d_rp);
+    // kernel variant: the smallest table whose sort holds the largest row
+    int64_t need = 1;
+    while (need < maxrow) need <<= 1;
+    b->variant = -1;
+    for (int v = 0; v < batch_variant_count(); ++v)
+        if (batch_variant_table(v) >= need) { b->variant = v; break; }
+    if (opt && opt->variant >= 0) {
+        if (opt->variant >= batch_variant_count() || batch_variant_table(opt->variant) < need)
+            return fail(SPGEMM_ERR_INVALID);
+        b->variant = opt->variant;
+    }
+    if (b->variant < 0) return fail(SPGEMM_ERR_INVALID);   // rows too large to batch
+    const int rg = 256 / batch_variant_lanes(b->variant);
+    b->tile_rows = (opt && opt->tile_rows > 0) ? opt->tile_rows : rg * 4;
+    if (b->tile_rows % rg) b->tile_rows += rg - b->tile_rows % rg;
+    b->spin_limit = (opt && opt->spin_limit > 0) ? opt->spin_limit : (1LL << 22);
+    // arena: per product C.rpt (M+1 int64), C.col and C.val with room for the bound
+    std::vector<size_t> off_rpt(n), off_col(n), off_val(n);
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        off_rpt[i] = total; total += align256(sizeof(int64_t) * (size_t)(b->M[i] + 1));
+        off_col[i] = total; total += align256(sizeof(int32_t) * (size_t)std::max<int64_t>(cap[i], 1));
+        off_val[i] = total; total += align256(sizeof(double) * (size_t)std::max<int64_t>(cap[i], 1));
+    }
+    b->arena = static_cast<unsigned char *>(dev_alloc(h, std::max<size_t>(total, 256)));
+    if (!b->arena) return fail(SPGEMM_ERR_OOM);
+    b->arena_bytes = total;
+    // problems and work items in dependency order
+    std::vector<BatchItem> items;
+    int maxlevel = 0;
+    for (int i = 0; i < n; ++i) maxlevel = std::max(maxlevel, level[i]);
+    for (int i = 0; i < n; ++i) {
+        BatchProb &P = b->probs[i];
+        const int dep = b_from ? b_from[i] : -1;
+        P.arpt = A[i].rpt; P.a64 = A[i].rpt_is_i64 ? 1 : 0; P.acol = A[i].col; P.aval = A[i].val;
+        P.M = b->M[i];
+        P.N = b->N[i];
+        P.crpt = reinterpret_cast<int64_t *>(b->arena + off_rpt[i]);
+        P.ccol = reinterpret_cast<int32_t *>(b->arena + off_col[i]);
+        P.cval = reinterpret_cast<double *>(b->arena + off_val[i]);
+        P.ccap = cap[i];
+        P.ntiles = static_cast<int32_t>((P.M + b->tile_rows - 1) / b->tile_rows);
+        P.dep = dep;
+        if (dep < 0) {
+            P.brpt = B[i].rpt; P.b64 = B[i].rpt_is_i64 ? 1 : 0; P.bcol = B[i].col; P.bval = B[i].val;
+        } else {
+            P.brpt = b->probs[dep].crpt; P.b64 = 1; P.bcol = b->probs[dep].ccol; P.bval = b->probs[dep].cval;
+        }
+    }
+    for (int L = 0; L <= maxlevel; ++L)
+        for (int type = 0; type < 3; ++type)
+            for (int i = 0; i < n; ++i) {
+                if (level[i] != L) continue;
+                if (type == 1) items.push_back({1, i, 0, 0});
+                else
+                    for (int t = 0; t < b->probs[i].ntiles; ++t) items.push_back({type, i, t, 0});
+            }
+    b->nitems = static_cast<int>(items.size());
+    b->d_probs = static_cast<BatchProb *>(dev_alloc(h, sizeof(BatchProb) * (size_t)std::max(n, 1)));
+    b->d_items = static_cast<BatchItem *>(dev_alloc(h, sizeof(BatchItem) * std::max<size_t>(items.size(), 1)));
+    b->state_bytes = sizeof(BatchState) + 3 * sizeof(int) * (size_t)std::max(n, 1);
+    b->d_state = static_cast<unsigned char *>(dev_alloc(h, b->state_bytes));
+    b->d_totals = static_cast<int64_t *>(dev_alloc(h, sizeof(int64_t) * (size_t)std::max(n, 1)));
+    if (!b->d_probs || !b->d_items || !b->d_state || !b->d_totals) return fail(SPGEMM_ERR_OOM);
+    if (n) CK(cudaMemcpyAsync(b->d_probs, b->probs.data(), sizeof(BatchProb) * (size_t)n,
+                              cudaMemcpyHostToDevice, h->stream));
+    if (!items.empty())
+        CK(cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(),
+                           cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    b->grid = std::max(1, h->sm_count * std::max(1, batch_blocks_per_sm(b->variant)));
+    // capture: reset the queue state, then the persistent kernel
+    cudaStream_t cs = h->side[0];
+    BatchState *st = reinterpret_cast<BatchState *>(b->d_state);
+    int *done_s = reinterpret_cast<int *>(b->d_state + sizeof(BatchState));
+    int *xflag = done_s + std::max(n, 1);
+    int *done_n = xflag + std::max(n, 1);
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = cudaMemsetAsync(b->d_state, 0, b->state_bytes, cs);
+    cudaError_t e2 = launch_batch(b->variant, b->grid, b->d_probs, b->d_items, b->nitems, st, done_s,
+                                  xflag, done_n, b->tile_rows, b->spin_limit, cs);
+    cudaError_t e3 = cudaStreamEndCapture(cs, &b->graph);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return fail(SPGEMM_ERR_CUDA);
+    CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    *out = b;
+    return SPGEMM_OK;
+}
+
+int spgemm_batch_run(spgemm_batch *b) {
+    if (!b) return SPGEMM_ERR_INVALID;
+    CK(cudaGraphLaunch(b->exec, b->h->stream));
+    return SPGEMM_OK;
+}
+
+int spgemm_batch_sync(spgemm_batch *b) {
+    if (!b) return SPGEMM_ERR_INVALID;
+    spgemm_handle *h = b->h;
+    BatchState host{};
+    if (b->n > 0) {
+        gather_totals_kernel<<<(b->n + 255) / 256, 256, 0, h->stream>>>(b->d_probs, b->n, b->d_totals);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(b->nnz.data(), b->d_totals, sizeof(int64_t) * (size_t)b->n,
+                           cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaMemcpyAsync(&host, b->d_state, sizeof(BatchState), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    b->last_rc = host.err;
+    return host.err;
+}
+
+int spgemm_batch_result(const spgemm_batch *b, int i, spgemm_csr_out *C) {
+    if (!b || !C || i < 0 || i >= b->n) return SPGEMM_ERR_INVALID;
+    const BatchProb &P = b->probs[i];
+    C->rows = P.M;
+    C->cols = P.N;
+    C->nnz = b->nnz[i];
+    C->rpt = P.crpt;
+    C->col = P.ccol;
+    C->val = P.cval;
+    return SPGEMM_OK;
+}
+
+int spgemm_batch_info(const spgemm_batch *b, int64_t *out, int nvals) {
+    if (!b || !out || nvals < 0) return SPGEMM_ERR_INVALID;
+    const int64_t v[6] = {b->n, b->nitems, b->grid, batch_variant_lanes(b->variant),
+                          batch_variant_table(b->variant), b->tile_rows};
+    for (int k = 0; k < std::min(nvals, 6); ++k) out[k] = v[k];
+    return SPGEMM_OK;
+}
+
+int spgemm_batch_destroy(spgemm_batch *b) {
+    if (!b) return SPGEMM_OK;
+    cudaStreamSynchronize(b->h->stream);
+    batch_release(b);
+    delete b;
     return SPGEMM_OK;
 }
 

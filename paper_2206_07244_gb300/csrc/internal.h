@@ -92,6 +92,39 @@ cudaError_t launch_num(int id, const Operands &op, const BinWork &w, size_t smem
 // one-phase numeric kernel `id` (a hash kernel of the numeric table)
 cudaError_t launch_num_onephase(int id, const Operands &op, const BinWork &w, cudaStream_t s);
 
+// --- batch.cu ------------------------------------------------------------------
+struct BatchProb {
+    const void *arpt; int a64; const int32_t *acol; const double *aval;
+    const void *brpt; int b64; const int32_t *bcol; const double *bval;
+    int64_t M, N;
+    int64_t *crpt; int32_t *ccol; double *cval; int64_t ccap;
+    int32_t ntiles;
+    int32_t dep;        // product whose C is this B, -1 when B is an input
+};
+
+struct BatchItem {
+    int32_t type;       // 0 symbolic tile, 1 scan, 2 numeric tile
+    int32_t prob;
+    int32_t tile;
+    int32_t pad;
+};
+
+// Device state, zeroed before every run: queue head, error word and where,
+// then per product: symbolic tiles done, scan done, numeric tiles done.
+struct BatchState {
+    unsigned long long head;
+    int err;
+    int where;
+};
+
+int batch_variant_count();
+int batch_variant_table(int v);
+int batch_variant_lanes(int v);
+int batch_blocks_per_sm(int variant);
+cudaError_t launch_batch(int variant, int grid, const BatchProb *probs, const BatchItem *items,
+                         int nitems, BatchState *st, int *done_s, int *xflag, int *done_n,
+                         int tile_rows, long long spin_limit, cudaStream_t s);
+
 // --- learned.cu ----------------------------------------------------------------
 int mlp_param_count();
 cudaError_t launch_features(const Operands &op, int64_t mrows, long long *nprod, unsigned *maxlen,
