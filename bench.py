@@ -172,6 +172,165 @@ def cpu_baseline(A, target_products=1.5e9):
                       f"dense-accumulator multiply, sort) on {threads} threads"}
 
 
+def _time_multiply(h, dA, r0, r1, reps=3):
+    import torch
+    for _ in range(1):
+        h.symbolic(dA, dA, r0, r1)
+        C = h.numeric(dA, dA)
+        del C
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h.symbolic(dA, dA, r0, r1)
+        C = h.numeric(dA, dA)
+        e1.record()
+        e1.synchronize()
+        del C
+        ts.append(e0.elapsed_time(e1))
+    h.status()
+    return float(np.median(ts))
+
+
+def learned_eval(workload_name, A, r0, r1):
+    """Plain vs learned sizing (trained weights) vs the n_prod upper bound
+    (a predictor that over-predicts every row) on rows [r0, r1) of A*A."""
+    import paper_2206_07244_gb300 as ops
+    from paper_2206_07244_gb300 import learned
+    man = json.load(open(learned.MANIFEST))
+    theta = np.load(learned.WEIGHTS)
+    dA = ops.CSR.from_workload(A)
+    out = {"workload": workload_name, "rows": [int(r0), int(r1)], "margin": man["margin"],
+           "val_mae_log1p": round(man["val_mae_log1p"], 4)}
+    with ops.Handle() as h:
+        t_plain = _time_multiply(h, dA, r0, r1)
+        st = h.stats()
+        nprod = st["total_nprod"]
+        out["nnzC"] = st["total_nnz"]
+        h.set_predictor(theta, man["margin"])
+        h.set_mode("learned")
+        t_learned = _time_multiply(h, dA, r0, r1)
+        out["learned_stats"] = h.learned_stats()
+        big = np.zeros_like(theta)
+        big[-1] = 30.0
+        h.set_predictor(big, 0.0)
+        t_bound = _time_multiply(h, dA, r0, r1)
+    g = lambda t: round(2.0 * nprod / (t / 1e3) / 1e9, 3)
+    out.update({"plain_ms": round(t_plain, 3), "learned_ms": round(t_learned, 3),
+                "nprod_bound_ms": round(t_bound, 3), "plain_gflops": g(t_plain),
+                "learned_gflops": g(t_learned), "nprod_bound_gflops": g(t_bound),
+                "learned_over_plain": round(t_plain / t_learned, 4),
+                "learned_over_nprod_bound": round(t_bound / t_learned, 4)})
+    return out
+
+
+def _product_bytes(arpt, acol, brpt, b_rpt_bytes, rows, nnzC):
+    """Compulsory bytes of one product: A's rows, the distinct B rows they
+    reference, and C (int64 row pointer)."""
+    a_bytes = arpt.itemsize * (rows + 1) + 12 * int(arpt[-1])
+    ks = np.unique(acol)
+    b_bytes = b_rpt_bytes * ks.size + 12 * int((brpt[ks + 1] - brpt[ks]).sum())
+    return a_bytes + b_bytes + 8 * (rows + 1) + 12 * int(nnzC)
+
+
+def batched_eval(count=512, seed=0, reps=3, tune=True):
+    """Multigrid Galerkin products P^T (A P) for `count` seeded grid sides
+    uniform in [8, 48] (A the 7-point Laplacian, P the 2x2x2 aggregation
+    prolongator); every product has its own device copy of its inputs.
+    Plain: 2 * count calls through the handle (A P, then P^T (A P)). Batched:
+    the same products in one persistent launch under a CUDA graph (default
+    and autotuned variant / rows per item). Times are wall-clock per whole
+    batch, from the first launch to the sizes on the host; the batch's
+    results are compared with the plain path's (exact: integer values)."""
+    import torch
+
+    import paper_2206_07244_gb300 as ops
+    from paper_2206_07244_gb300 import autotune
+    from paper_2206_07244_gb300.batch import Batch, galerkin_batch
+    sides = W.galerkin_sides(count, seed=seed)
+    peak, peak_kind = peaks()
+    host = {int(s): W.galerkin_problem(int(s)) for s in np.unique(sides)}
+    out = {"workload": f"{count} Galerkin products P^T(A P), A = 7-point Laplacian on s^3, "
+                       f"s uniform in [8, 48] (seed {seed}), P = 2x2x2 aggregation; "
+                       "inputs copied per product",
+           "sides_sum_rows": int(sum(int(s) ** 3 for s in sides))}
+    with ops.Handle() as h:
+        As, Bs, dep, inputs = galerkin_batch(h, sides, share_inputs=False)
+
+        def plain_once(keep=False):
+            kept = []
+            for A, P, PT in inputs:
+                C1 = h.multiply(A, P)
+                C2 = h.multiply(PT, C1)
+                if keep:
+                    kept.append((C1.rpt.cpu().numpy(), C1.nnz, C2))
+                del C1
+            return kept
+
+        kept = plain_once(keep=True)
+        h.status()
+        nprod = 0
+        bytes_ = 0
+        for i, s in enumerate(sides):
+            A, P, PT = host[int(s)]
+            rpt1, nnz1, C2 = kept[i]
+            nprod += int(np.diff(P.rpt)[A.col].sum()) + int(np.diff(rpt1)[PT.col].sum())
+            bytes_ += _product_bytes(A.rpt, A.col, P.rpt.astype(np.int64), 4, A.rows, nnz1)
+            bytes_ += _product_bytes(PT.rpt, PT.col, rpt1, 8, PT.rows, C2.nnz)
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plain_once()
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        t_plain = float(np.median(ts))
+        with Batch(h, As, Bs, dep) as b:
+            t_batch = autotune.time_batch(b, reps)
+            info = b.info()
+            match = True
+            for i in range(count):
+                C = b.result(count + i)
+                ref = kept[i][2]
+                match &= (C.nnz == ref.nnz and torch.equal(C.rpt, ref.rpt) and torch.equal(C.col, ref.col)
+                          and torch.equal(C.val, ref.val))
+        best = hist = None
+        if tune:
+            best, hist = autotune.tune_batch(h, As, Bs, dep, reps=reps)
+            with Batch(h, As, Bs, dep, variant=best["variant"], tile_rows=best["tile_rows"]) as b:
+                t_tuned = autotune.time_batch(b, reps)
+    g = lambda t: round(2.0 * nprod / (t / 1e3) / 1e9, 3)
+    bw = lambda t: round(bytes_ / (t / 1e3) / 1e9, 1)
+    out.update({"nprod": nprod, "compulsory_bytes": bytes_, "plain_calls": 2 * count,
+                "plain_ms": round(t_plain, 3), "batched_ms": round(t_batch, 3),
+                "plain_gflops": g(t_plain), "batched_gflops": g(t_batch),
+                "batched_over_plain": round(t_plain / t_batch, 3),
+                "batched_gbs": bw(t_batch), "batched_hbm_frac": round(bw(t_batch) / peak, 4),
+                "peak_gbs": peak, "peak_kind": peak_kind, "batch_info": info,
+                "batch_matches_plain": bool(match)})
+    if best is not None:
+        out.update({"tuned": best, "tuned_ms": round(t_tuned, 3), "tuned_gflops": g(t_tuned),
+                    "tuned_gbs": bw(t_tuned), "tuned_hbm_frac": round(bw(t_tuned) / peak, 4),
+                    "tuned_over_plain": round(t_plain / t_tuned, 3), "tune_trials": len(hist)})
+    return out
+
+
+def pick_slab(A, budget_entries):
+    """A contiguous row slab of A*A, starting at row A.rows/2, whose C has at
+    most budget_entries entries (sized with the library's symbolic phase)."""
+    import paper_2206_07244_gb300 as ops
+    dA = ops.CSR.from_workload(A)
+    r0 = A.rows // 2
+    r1 = A.rows
+    with ops.Handle() as h:
+        while r1 - r0 > 1024:
+            nnz = h.symbolic(dA, dA, r0, r1)
+            if nnz <= budget_entries:
+                break
+            r1 = r0 + (r1 - r0) // 2
+    return r0, r1
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -214,6 +373,10 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="also tune the bin configuration and time plain vs tuned")
     ap.add_argument("--save-config", default=None)
+    ap.add_argument("--learned", action="store_true",
+                    help="also compare learned sizing with the plain path (trained weights)")
+    ap.add_argument("--batched", action="store_true",
+                    help="also run the 512 Galerkin products plain vs batched (autotuned)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not os.environ.get("BENCH_ALLOW_SHORT"):
         args.warmup = 3
@@ -366,6 +529,24 @@ def main():
     if not args.no_cpu_baseline and rank == 0 and ws == 1:
         cpu = cpu_baseline(A)
 
+    learned_legs = batched = None
+    legs = (args.learned or args.batched) and rank == 0
+    if legs:
+        h.close()
+        del dA
+        torch.cuda.empty_cache()
+    if args.batched and rank == 0:
+        batched = batched_eval()
+        torch.cuda.empty_cache()
+    if args.learned and rank == 0:
+        learned_legs = []
+        R = W.rmat(21, 32, seed=2021)
+        r0, r1 = pick_slab(R, 2_000_000_000)
+        learned_legs.append(learned_eval("held-out R-MAT n=2^21, degree 32, seed 2021", R, r0, r1))
+        del R
+        S = W.stencil27(128, seed=3)
+        learned_legs.append(learned_eval("27-point stencil 128^3", S, 0, S.rows))
+
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "GFLOPS", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup,
@@ -379,11 +560,12 @@ def main():
                            "bin_config": "autotuned" if args.config else "default"},
                 "roofline": roofline, "roofline_whole_step": whole,
                 "stage_ms_live": breakdown, "kernel_ms_serial": serial,
-                "bins": bins, "autotune": tuned,
+                "bins": bins, "autotune": tuned, "learned": learned_legs, "batched": batched,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
-    h.close()
+    if not legs:
+        h.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

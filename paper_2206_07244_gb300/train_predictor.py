@@ -1,0 +1,143 @@
+"""Train the row-size predictor on 200 seeded matrices and save it.
+
+    python -m paper_2206_07244_gb300.train_predictor [--out DIR] [--epochs E]
+
+Training set (seeds 1000 + index):
+  - 67 banded matrices, n = 2^16, half-bandwidth uniform in [1, 32]
+    (bandwidth 3-65);
+  - 67 R-MAT graphs, n = 2^16, 2^17 or 2^18, degree uniform in [8, 32];
+  - 66 random block-diagonal matrices, n = 2^16, 32-256 blocks, mean degree
+    uniform in [8, 32];
+all with values uniform in [-1, 1], C = A*A. Labels are log1p of the exact
+row sizes the two-phase method computes on the GPU; at most 4096 rows per
+matrix are kept, stratified by n_prod. Every tenth matrix is held out for
+validation; the safety margin of the predicted sizes is the smallest of a
+grid for which at most 1% of validation rows would overflow the table of
+the bin their predicted size selects (each numeric table already holds
+twice its bin's range). Forward,
+backward and Adam run in the library's CUDA kernels.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+
+def matrix_recipe(idx: int):
+    """(kind, params) of training matrix idx in [0, 200)."""
+    seed = 1000 + idx
+    rng = np.random.default_rng(seed)
+    if idx < 67:
+        return "banded", {"n": 1 << 16, "half_bw": int(rng.integers(1, 33)), "seed": seed}
+    if idx < 134:
+        return "rmat", {"scale": int(rng.integers(16, 19)), "degree": int(rng.integers(8, 33)),
+                        "seed": seed}
+    return "block", {"n": 1 << 16, "nblocks": int(rng.integers(32, 257)),
+                     "mean_degree": float(rng.uniform(8, 32)), "seed": seed}
+
+
+def build_matrix(kind, p):
+    import workloads as W
+    if kind == "banded":
+        return W.banded(p["n"], p["half_bw"], p["seed"])
+    if kind == "rmat":
+        return W.rmat(p["scale"], p["degree"], seed=p["seed"])
+    return W.block_diagonal(p["n"], p["nblocks"], p["mean_degree"], p["seed"])
+
+
+def under_rate(pred_log, true_nnz, margin):
+    """Rows whose predicted size (with the margin) is below the true size."""
+    size = np.maximum(np.ceil(np.expm1(pred_log) * (1.0 + margin)), 1.0)
+    return float(np.mean(size < true_nnz))
+
+
+def overflow_rate(pred_log, true_nnz, margin, ranges, capacities):
+    """Rows the learned mode would have to recompute: the bin chosen by the
+    predicted size (first range >= size) cannot hold the true row size
+    (its table holds up to `capacity` keys; sizes past the last range go to
+    the exact path and never overflow)."""
+    size = np.maximum(np.ceil(np.expm1(pred_log) * (1.0 + margin)), 1.0)
+    j = np.searchsorted(np.asarray(ranges), size, side="left")
+    cap = np.append(np.asarray(capacities, dtype=np.float64), np.inf)[j]
+    return float(np.mean(true_nnz > cap))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--matrices", type=int, default=200)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    args = ap.parse_args(argv)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import torch
+
+    from . import CSR, Handle
+    from . import learned
+
+    t0 = time.time()
+    train_pairs, val_pairs = [], []
+    recipes = []
+    with Handle() as h:
+        Xs, ts, Xv, tv = [], [], [], []
+        for idx in range(args.matrices):
+            kind, p = matrix_recipe(idx)
+            recipes.append({"kind": kind, **p})
+            A = build_matrix(kind, p)
+            dA = CSR.from_workload(A)
+            X, t = learned.training_set([(dA, dA)], rows_per_matrix=4096, seed=idx, handle=h)
+            (Xv if idx % 10 == 9 else Xs).append(X)
+            (tv if idx % 10 == 9 else ts).append(t)
+        gen_s = time.time() - t0
+    X, t = torch.cat(Xs), torch.cat(ts)
+    Xval, tval = torch.cat(Xv), torch.cat(tv)
+    pred = learned.Predictor(seed=0)
+    t1 = time.time()
+    hist = pred.fit(X, t, epochs=args.epochs, batch=args.batch, lr=args.lr, seed=0)
+    train_s = time.time() - t1
+    yv = pred.forward(Xval).cpu().numpy().astype(np.float64)
+    nz = np.expm1(tval.cpu().numpy().astype(np.float64)).round()
+    mae = float(np.mean(np.abs(yv - tval.cpu().numpy())))
+    # numeric hash bins of the default configuration: a row predicted to
+    # have `size` entries goes to the first bin whose range holds it, and
+    # overflows only if its true size passes that table's capacity
+    from . import kernel_table
+    with Handle() as hh:
+        cfg = hh.get_config()
+    tab = kernel_table(1)
+    ranges = cfg["num_range"][:-1]
+    caps = [tab[k][3] for k in cfg["num_kernel"][:-1]]
+    margin = None
+    for m in (0.0, 0.05, 0.1, 0.15, 0.2, 0.3, 0.4, 0.5, 0.75, 1.0, 1.5, 2.0):
+        if overflow_rate(yv, nz, m, ranges, caps) <= 0.01:
+            margin = m
+            break
+    margin = 2.0 if margin is None else margin
+    manifest = {"recipe": "see paper_2206_07244_gb300/train_predictor.py",
+                "matrices": recipes, "init_seed": 0, "epochs": args.epochs, "batch": args.batch,
+                "lr": args.lr, "train_rows": int(X.shape[0]), "val_rows": int(Xval.shape[0]),
+                "loss_history": hist, "val_mae_log1p": mae, "margin": margin,
+                "val_overflow_rate_at_margin": overflow_rate(yv, nz, margin, ranges, caps),
+                "val_under_rate_at_margin": under_rate(yv, nz, margin),
+                "val_under_rate_no_margin": under_rate(yv, nz, 0.0),
+                "seconds_generate_and_label": round(gen_s, 1), "seconds_train": round(train_s, 1)}
+    out = args.out or os.path.dirname(learned.WEIGHTS)
+    os.makedirs(out, exist_ok=True)
+    np.save(os.path.join(out, "weights.npy"), pred.theta.cpu().numpy())
+    with open(os.path.join(out, "manifest.json"), "w") as f:
+        json.dump(manifest, f, indent=1)
+    print(json.dumps({k: v for k, v in manifest.items() if k not in ("matrices", "loss_history")}))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
