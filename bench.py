@@ -50,7 +50,9 @@ WORKLOADS = {
 }
 
 SLOT_NAMES = ([f"sym_bin{j}" for j in range(16)] + [f"num_bin{j}" for j in range(16)]
-              + ["nprod", "sym_pass1", "sym_pass2", "num_pass1", "num_pass2", "scan"])
+              + ["nprod", "sym_pass1", "sym_pass2", "num_pass1", "num_pass2", "scan",
+                 "features", "mlp_sizes", "copy_rows"])
+NSLOTS = len(SLOT_NAMES)
 
 
 def peaks():
@@ -192,6 +194,25 @@ def _time_multiply(h, dA, r0, r1, reps=3):
     return float(np.median(ts))
 
 
+def _serial_breakdown(h, dA, r0, r1):
+    """Per-kernel milliseconds of one multiply with every kernel on one
+    stream (untimed step; events around each launch)."""
+    import ctypes
+
+    from paper_2206_07244_gb300 import _abi
+    lib = _abi.lib()
+    ms_arr = (ctypes.c_double * NSLOTS)()
+    ln_arr = (ctypes.c_int64 * NSLOTS)()
+    _abi.check(lib.spgemm_set_timing(h._h, 2), "spgemm_set_timing")
+    _abi.check(lib.spgemm_kernel_times(h._h, ms_arr, ln_arr, NSLOTS, 1), "spgemm_kernel_times")
+    h.symbolic(dA, dA, r0, r1)
+    C = h.numeric(dA, dA)
+    del C
+    _abi.check(lib.spgemm_kernel_times(h._h, ms_arr, ln_arr, NSLOTS, 1), "spgemm_kernel_times")
+    lib.spgemm_set_timing(h._h, 0)
+    return {SLOT_NAMES[i]: round(ms_arr[i], 3) for i in range(NSLOTS) if ms_arr[i] > 0}
+
+
 def learned_eval(workload_name, A, r0, r1):
     """Plain vs learned sizing (trained weights) vs the n_prod upper bound
     (a predictor that over-predicts every row) on rows [r0, r1) of A*A."""
@@ -207,10 +228,12 @@ def learned_eval(workload_name, A, r0, r1):
         st = h.stats()
         nprod = st["total_nprod"]
         out["nnzC"] = st["total_nnz"]
+        out["plain_kernel_ms_serial"] = _serial_breakdown(h, dA, r0, r1)
         h.set_predictor(theta, man["margin"])
         h.set_mode("learned")
         t_learned = _time_multiply(h, dA, r0, r1)
         out["learned_stats"] = h.learned_stats()
+        out["learned_kernel_ms_serial"] = _serial_breakdown(h, dA, r0, r1)
         big = np.zeros_like(theta)
         big[-1] = 30.0
         h.set_predictor(big, 0.0)
@@ -422,9 +445,9 @@ def main():
     nprod_slab = stats["total_nprod"]
 
     _abi.check(lib.spgemm_set_timing(h._h, 1), "spgemm_set_timing")
-    ms_arr = (ctypes.c_double * 38)()
-    ln_arr = (ctypes.c_int64 * 38)()
-    _abi.check(lib.spgemm_kernel_times(h._h, ms_arr, ln_arr, 38, 1), "spgemm_kernel_times")
+    ms_arr = (ctypes.c_double * NSLOTS)()
+    ln_arr = (ctypes.c_int64 * NSLOTS)()
+    _abi.check(lib.spgemm_kernel_times(h._h, ms_arr, ln_arr, NSLOTS, 1), "spgemm_kernel_times")
 
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -438,7 +461,7 @@ def main():
         barrier()
     h.status()
     ms = ev0.elapsed_time(ev1)
-    _abi.check(lib.spgemm_kernel_times(h._h, ms_arr, ln_arr, 38, 1), "spgemm_kernel_times")
+    _abi.check(lib.spgemm_kernel_times(h._h, ms_arr, ln_arr, NSLOTS, 1), "spgemm_kernel_times")
     kms = list(ms_arr)
     kln = list(ln_arr)
     # Bins of one phase run concurrently on side streams, so a small bin's
@@ -449,7 +472,7 @@ def main():
     for _ in range(2):
         C = step()
         del C
-    _abi.check(lib.spgemm_kernel_times(h._h, ms_arr, ln_arr, 38, 1), "spgemm_kernel_times")
+    _abi.check(lib.spgemm_kernel_times(h._h, ms_arr, ln_arr, NSLOTS, 1), "spgemm_kernel_times")
     lib.spgemm_set_timing(h._h, 0)
     sms_ = list(ms_arr)
     sln = list(ln_arr)

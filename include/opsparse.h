@@ -90,7 +90,15 @@ typedef void (*spgemm_free_fn)(void *ptr, void *stream, void *ctx);
  * together in the symbolic / numeric phase (1..32, a power of two), or 0 to
  * pick it per output row from the mean referenced B-row length.
  * bitmap_unroll: products each thread of a bitmap kernel loads before using
- * them (4 or 8; 0 = 4). */
+ * them (4 or 8; 0 = 4).
+ * window_lists (0..1024, 0 = off, the default): when every row of B is
+ * sorted by column and B's columns fit one bitmap, rows of the numeric
+ * bitmap kernel with at most this many A entries (and at most as many as
+ * the kernel's block has threads) sum their values window by window over
+ * the column space, so that the C.val lines being summed into stay in L2.
+ * This halves that kernel's DRAM traffic on power-law inputs but executes
+ * more instructions per product. window_entries: C entries per such window,
+ * about (0 = 12288). */
 typedef struct {
     int32_t sym_nbins;
     int32_t sym_kernel[SPGEMM_MAX_BINS];
@@ -101,7 +109,9 @@ typedef struct {
     int32_t lanes_per_brow;
     int32_t num_lanes_per_brow;
     int32_t bitmap_unroll;
-    int32_t reserved[5];
+    int32_t window_lists;
+    int32_t window_entries;
+    int32_t reserved[3];
 } spgemm_config;
 
 typedef struct spgemm_handle spgemm_handle;
@@ -191,8 +201,10 @@ int spgemm_bin_stats(const spgemm_handle *h, int phase, int64_t *out, int n);
  * launched on. spgemm_kernel_times synchronises the handle's stream and
  * returns accumulated milliseconds and launch counts per slot: slots 0-15
  * the symbolic bins, 16-31 the numeric bins, 32 n_prod, 33/34 symbolic
- * binning passes 1/2, 35/36 numeric binning passes 1/2, 37 the scan
- * (38 slots). reset != 0 clears the totals. */
+ * binning passes 1/2, 35/36 numeric binning passes 1/2, 37 the scan; in
+ * learned mode also 38 the row features, 39 the MLP forward with the sizes
+ * and binning by prediction, 40 the copy of one-phase rows into C (41
+ * slots). reset != 0 clears the totals. */
 int spgemm_set_timing(spgemm_handle *h, int enable);
 int spgemm_kernel_times(spgemm_handle *h, double *ms, int64_t *launches, int n,
                         int reset);
@@ -302,6 +314,11 @@ int spgemm_batch_info(const spgemm_batch *b, int64_t *out, int n);
 int spgemm_batch_destroy(spgemm_batch *b);
 
 const char *spgemm_strerror(int code);
+/* Name of the last CUDA runtime error that the library, on the calling
+ * thread, turned into SPGEMM_ERR_CUDA or SPGEMM_ERR_OOM (e.g.
+ * "cudaErrorInvalidValue"), or NULL if there was none. Diagnostic only; a
+ * static string. */
+const char *spgemm_last_cuda_error(void);
 
 /* ---- Sizing C without allocating device memory --------------------------
  * The paper has no counterpart to this function; it serves callers that

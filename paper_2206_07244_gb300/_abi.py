@@ -20,6 +20,7 @@ EXPORTS = [
     "spgemm_create", "spgemm_set_config", "spgemm_get_config", "spgemm_symbolic",
     "spgemm_numeric", "spgemm_multiply", "spgemm_status", "spgemm_free",
     "spgemm_destroy", "spgemm_last_stats", "spgemm_kernel_info", "spgemm_strerror",
+    "spgemm_last_cuda_error",
     "spgemm_multiply_host", "spgemm_bin_stats", "spgemm_set_timing", "spgemm_kernel_times",
     "spgemm_rowptr_noalloc", "spgemm_mlp_param_count", "spgemm_set_predictor", "spgemm_set_mode",
     "spgemm_learned_stats", "spgemm_features", "spgemm_mlp_forward", "spgemm_mlp_train_step",
@@ -29,9 +30,11 @@ EXPORTS = [
 
 
 class SpgemmError(RuntimeError):
-    def __init__(self, code: int, where: str):
+    def __init__(self, code: int, where: str, cuda: str | None = None):
         self.code = code
-        super().__init__(f"{where}: {ERRORS.get(code, code)}")
+        self.cuda = cuda
+        extra = f" ({cuda})" if cuda else ""
+        super().__init__(f"{where}: {ERRORS.get(code, code)}{extra}")
 
 
 class CsrIn(ctypes.Structure):
@@ -56,7 +59,8 @@ class Config(ctypes.Structure):
                 ("num_nbins", ctypes.c_int32), ("num_kernel", ctypes.c_int32 * MAX_BINS),
                 ("num_range", ctypes.c_int64 * MAX_BINS),
                 ("lanes_per_brow", ctypes.c_int32), ("num_lanes_per_brow", ctypes.c_int32),
-                ("bitmap_unroll", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("bitmap_unroll", ctypes.c_int32), ("window_lists", ctypes.c_int32),
+                ("window_entries", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -121,13 +125,19 @@ def lib(path: str | None = None):
             f.restype = ctypes.c_int
         L.spgemm_strerror.argtypes = [ctypes.c_int]
         L.spgemm_strerror.restype = ctypes.c_char_p
+        L.spgemm_last_cuda_error.argtypes = []
+        L.spgemm_last_cuda_error.restype = ctypes.c_char_p
         _lib = L
         return _lib
 
 
 def check(rc: int, where: str):
     if rc != 0:
-        raise SpgemmError(rc, where)
+        cuda = None
+        if rc in (-3, -6) and _lib is not None:
+            name = _lib.spgemm_last_cuda_error()
+            cuda = name.decode() if name else None
+        raise SpgemmError(rc, where, cuda)
 
 
 def kernel_table(phase: int):
@@ -152,7 +162,8 @@ def config_to_dict(c: Config) -> dict:
             "num_range": list(c.num_range[:c.num_nbins]),
             "lanes_per_brow": int(c.lanes_per_brow),
             "num_lanes_per_brow": int(c.num_lanes_per_brow),
-            "bitmap_unroll": int(c.bitmap_unroll)}
+            "bitmap_unroll": int(c.bitmap_unroll),
+            "window_lists": int(c.window_lists), "window_entries": int(c.window_entries)}
 
 
 def config_from_dict(d: dict) -> Config:
@@ -170,4 +181,6 @@ def config_from_dict(d: dict) -> Config:
     c.lanes_per_brow = int(d.get("lanes_per_brow", 0))
     c.num_lanes_per_brow = int(d.get("num_lanes_per_brow", 0))
     c.bitmap_unroll = int(d.get("bitmap_unroll", 0))
+    c.window_lists = int(d.get("window_lists", 0))
+    c.window_entries = int(d.get("window_entries", 0))
     return c

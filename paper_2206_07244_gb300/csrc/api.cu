@@ -44,10 +44,23 @@ enum Slot {
     kSlotNumPass1 = 35,
     kSlotNumPass2 = 36,
     kSlotScan = 37,
-    kSlots = 38,
+    kSlotFeatures = 38,   // learned mode: row features
+    kSlotMlp = 39,        // learned mode: MLP forward, sizes, binning by prediction
+    kSlotCopy = 40,       // learned mode: one-phase rows copied into C
+    kSlots = 41,
 };
 
 }  // namespace
+
+// Pass 2 of the numeric bitmap kernel by column windows: rows with at most
+// `lists` A entries (0: not used), G sub-ranges of 2^gshift columns, about
+// `entries` C entries per window.
+struct RunPlan {
+    int lists = 0;
+    int G = 0, gshift = 0;
+    int entries = 0;
+    const int32_t *bs = nullptr;     // run boundaries of B rows (set by the numeric phase)
+};
 
 struct spgemm_handle {
     int device = 0;
@@ -72,6 +85,8 @@ struct spgemm_handle {
     int64_t row0 = 0, mw = 0, ncols = 0, nnz = 0;
     int64_t *crpt = nullptr;
     long long num_size[kMaxBins] = {};
+    RunPlan rplan;               // windowed pass 2 plan of the last symbolic call
+    bool b_unsorted = false;     // some row of B has decreasing columns
     int64_t stats[4 + 2 * SPGEMM_MAX_BINS] = {};
     int64_t bin_stats[2][3 * SPGEMM_MAX_BINS] = {};
     // learned sizing
@@ -230,6 +245,7 @@ int validate_config(const spgemm_config &c) {
     if (!is_pow2_lanes(c.lanes_per_brow) || !is_pow2_lanes(c.num_lanes_per_brow))
         return SPGEMM_ERR_INVALID;
     if (c.bitmap_unroll != 0 && c.bitmap_unroll != 4 && c.bitmap_unroll != 8) return SPGEMM_ERR_INVALID;
+    if (c.window_lists < 0 || c.window_lists > kWinMaxLists || c.window_entries < 0) return SPGEMM_ERR_INVALID;
     for (int phase = 0; phase < 2; ++phase) {
         const int nb = phase ? c.num_nbins : c.sym_nbins;
         const int32_t *k = phase ? c.num_kernel : c.sym_kernel;
@@ -300,7 +316,32 @@ void auto_cut(spgemm_config &c, int64_t ncols) {
     }
 }
 
+RunPlan run_plan(const spgemm_config &c, int smem_dyn_max, int64_t ncols) {
+    RunPlan p;
+    if (c.window_lists <= 0 || ncols <= 0) return p;
+    // the whole column range must fit one bitmap window next to the run metadata
+    const int64_t words = (ncols + 63) / 64;
+    if (words * 12 > smem_dyn_max - static_cast<int64_t>(num_bitmap_head_bytes(true))) return p;
+    int gshift = 6;
+    while (((ncols + (int64_t{1} << gshift) - 1) >> gshift) > kRunMaxSub) ++gshift;
+    p.lists = c.window_lists;
+    p.gshift = gshift;
+    p.G = static_cast<int>((ncols + (int64_t{1} << gshift) - 1) >> gshift);
+    p.entries = c.window_entries > 0 ? c.window_entries : kRunDefaultEntries;
+    return p;
+}
+
+// Last CUDA runtime error the library turned into an error code on this
+// thread (spgemm_last_cuda_error).
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+cudaError_t note(cudaError_t e) {
+    if (e != cudaSuccess) g_last_cuda = e;
+    return e;
+}
+
 int cuda_rc(cudaError_t e) {
+    note(e);
     if (e == cudaSuccess) return SPGEMM_OK;
     if (e == cudaErrorMemoryAllocation) return SPGEMM_ERR_OOM;
     return SPGEMM_ERR_CUDA;
@@ -329,9 +370,11 @@ Operands make_operands(const spgemm_csr_in *A, const spgemm_csr_in *B, int64_t r
 }
 
 // Launch the kernels of one phase, one per non-empty bin, largest rows first,
-// spread over the side streams.
+// spread over the side streams. runs: plan of a windowed pass 2 for the
+// numeric bitmap kernel (nullptr or runs->lists == 0: whole-row pass 2).
 int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *size,
-             const long long *offset, bool identity, int64_t *crpt, int32_t *ccol, double *cval) {
+             const long long *offset, bool identity, int64_t *crpt, int32_t *ccol, double *cval,
+             const RunPlan *runs = nullptr) {
     const int nb = phase ? h->cfg.num_nbins : h->cfg.sym_nbins;
     const int32_t *kid = phase ? h->cfg.num_kernel : h->cfg.sym_kernel;
     CK(cudaEventRecord(h->ev_fork, h->stream));
@@ -340,7 +383,7 @@ int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *s
         if (size[j] <= 0) continue;
         cudaStream_t s = h->serial ? h->stream : h->side[used % kSide];
         if (!h->serial && used < kSide) CK(cudaStreamWaitEvent(s, h->ev_fork, 0));
-        BinWork w;
+        BinWork w{};
         w.bins = identity ? nullptr : d_bins(h);
         w.off = identity ? 0 : offset[j];
         w.cnt = size[j];
@@ -351,12 +394,21 @@ int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *s
         const KernelDesc &d = phase ? num_kernel(kid[j]) : sym_kernel(kid[j]);
         size_t smem = 0;
         if (d.bitmap) {
-            // bitmap bytes; the kernels add their walk scratch on top
-            const int64_t budget = h->smem_dyn_max - static_cast<int64_t>(sizeof(WalkScratch));
+            // bitmap bytes; the kernels add their head (walk scratch / run metadata)
             if (phase == 0) {
+                const int64_t budget = h->smem_dyn_max - static_cast<int64_t>(sizeof(WalkScratch));
                 const int64_t words = std::min<int64_t>((op.ncols + 31) / 32, budget / 4);
                 smem = static_cast<size_t>(std::max<int64_t>(words, 1)) * 4;
             } else {
+                const bool r = runs && runs->lists > 0 && runs->bs;
+                if (r) {
+                    w.bs = runs->bs;
+                    w.G = runs->G;
+                    w.gshift = runs->gshift;
+                    w.wlists = runs->lists;
+                    w.wentries = runs->entries;
+                }
+                const int64_t budget = h->smem_dyn_max - static_cast<int64_t>(num_bitmap_head_bytes(r));
                 const int64_t words = std::min<int64_t>((op.ncols + 63) / 64, budget / 12);
                 smem = static_cast<size_t>(std::max<int64_t>(words, 1)) * 12;
             }
@@ -422,7 +474,10 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
     long long *fnp = reinterpret_cast<long long *>(L.fws);
     unsigned *fmx = reinterpret_cast<unsigned *>(L.fws + sizeof(long long) * (size_t)mw);
     unsigned *fmn = fmx + mw;
+    time_begin(h, kSlotFeatures, s);
     CK(launch_features(op, mrows, fnp, fmx, fmn, L.X, h->sm_count * 8, s));
+    time_end(h, kSlotFeatures, s);
+    time_begin(h, kSlotMlp, s);
     CK(launch_mlp_forward(h->theta, L.X, mw, nullptr, L.pred, h->margin, cap + 1, s));
     const int64_t exact_above = h->cfg.sym_nbins >= 2 ? h->cfg.sym_range[h->cfg.sym_nbins - 2] : -1;
     CK(launch_learned_sizes(crpt, L.pred, mw, exact_above, LLONG_MAX / 4, L.lsizes, s));
@@ -430,6 +485,7 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
     rn.nb = nb;
     for (int j = 0; j < nb; ++j) rn.r[j] = h->cfg.num_range[j];
     CK(launch_bin_pass1(L.lsizes, mw, rn, op, d_counters(h, 0), nullptr, s));
+    time_end(h, kSlotMlp, s);
     if ((rc = read_counters(h))) return rc;
     h->lid = plan_bins(h->h_cnt[0], nb, h->lsize, h->loff);
     if (!h->lid) CK(launch_bin_pass2(L.lsizes, mw, rn, h->loff, d_counters(h, 0), d_bins(h), s));
@@ -539,6 +595,7 @@ int numeric_learned(spgemm_handle *h, const Operands &op, int64_t *crpt, int32_t
         if (!*pcol || !*pval) return SPGEMM_ERR_OOM;
     }
     const int last = h->cfg.num_nbins - 1;
+    time_begin(h, kSlotCopy, s);
     for (int j = 0; j < last; ++j) {
         if (h->lsize[j] <= 0) continue;
         BinWork w{};
@@ -553,6 +610,7 @@ int numeric_learned(spgemm_handle *h, const Operands &op, int64_t *crpt, int32_t
         w.err = d_err(h);
         CK(launch_copy_rows(w, s));
     }
+    time_end(h, kSlotCopy, s);
     if (h->xcount > 0) {
         BinWork w{};
         w.bins = L.xlist; w.off = 0; w.cnt = h->xcount;
@@ -560,7 +618,7 @@ int numeric_learned(spgemm_handle *h, const Operands &op, int64_t *crpt, int32_t
         w.lanes = h->cfg.num_lanes_per_brow;
         w.unroll = h->cfg.bitmap_unroll;
         w.err = d_err(h);
-        const int64_t budget = h->smem_dyn_max - static_cast<int64_t>(sizeof(WalkScratch));
+        const int64_t budget = h->smem_dyn_max - static_cast<int64_t>(num_bitmap_head_bytes(false));
         const int64_t words = std::min<int64_t>((op.ncols + 63) / 64, budget / 12);
         time_begin(h, kSlotNumBin + 15, s);
         CK(launch_num(num_kernel_count() - 1, op, w, static_cast<size_t>(std::max<int64_t>(words, 1)) * 12, s));
@@ -576,6 +634,10 @@ int numeric_learned(spgemm_handle *h, const Operands &op, int64_t *crpt, int32_t
 }  // namespace
 
 extern "C" {
+
+const char *spgemm_last_cuda_error(void) {
+    return g_last_cuda == cudaSuccess ? nullptr : cudaGetErrorName(g_last_cuda);
+}
 
 const char *spgemm_strerror(int code) {
     switch (code) {
@@ -710,13 +772,13 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
         return code;
     };
     // zero both phases' counters, keep the error word
-    if (cudaMemsetAsync(h->arena, 0, 2 * sizeof(Counters), h->stream) != cudaSuccess ||
-        cudaMemsetAsync(crpt, 0, sizeof(int64_t) * (size_t)(mw + 1), h->stream) != cudaSuccess)
+    if (note(cudaMemsetAsync(h->arena, 0, 2 * sizeof(Counters), h->stream)) != cudaSuccess ||
+        note(cudaMemsetAsync(crpt, 0, sizeof(int64_t) * (size_t)(mw + 1), h->stream)) != cudaSuccess)
         return fail(SPGEMM_ERR_CUDA);
     const Operands op = make_operands(A, B, row_begin, mw);
     // step 1: n_prod per row into C.rpt
     time_begin(h, kSlotNprod, h->stream);
-    if (launch_nprod(op, crpt, h->sm_count * 8, h->stream) != cudaSuccess) return fail(SPGEMM_ERR_CUDA);
+    if (note(launch_nprod(op, crpt, h->sm_count * 8, h->stream)) != cudaSuccess) return fail(SPGEMM_ERR_CUDA);
     time_end(h, kSlotNprod, h->stream);
     if (h->mode == SPGEMM_MODE_LEARNED) {
         // the one-phase kernels multiply during this call: they read values
@@ -741,12 +803,18 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
         *nnzC = nnz;
         return SPGEMM_OK;
     }
+    // rows of B must be sorted for the windowed pass 2 of the numeric bitmap kernel
+    h->rplan = run_plan(h->cfg, h->smem_dyn_max, B->cols);
+    if (h->rplan.lists > 0 &&
+        note(launch_sorted_check(op, B->rows, B->nnz, d_counters(h, 1), h->sm_count * 4, h->stream)) !=
+            cudaSuccess)
+        return fail(SPGEMM_ERR_CUDA);
     // step 2: symbolic binning by n_prod
     Ranges rs{};
     rs.nb = h->cfg.sym_nbins;
     for (int j = 0; j < rs.nb; ++j) rs.r[j] = h->cfg.sym_range[j];
     time_begin(h, kSlotSymPass1, h->stream);
-    if (launch_bin_pass1(crpt, mw, rs, op, d_counters(h, 0), nullptr, h->stream) != cudaSuccess)
+    if (note(launch_bin_pass1(crpt, mw, rs, op, d_counters(h, 0), nullptr, h->stream)) != cudaSuccess)
         return fail(SPGEMM_ERR_CUDA);
     time_end(h, kSlotSymPass1, h->stream);
     if ((rc = read_counters(h))) return fail(rc);
@@ -757,7 +825,7 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     for (int j = 0; j < SPGEMM_MAX_BINS; ++j) h->stats[4 + j] = j < rs.nb ? ssize[j] : 0;
     if (!sid) {
         time_begin(h, kSlotSymPass2, h->stream);
-        if (launch_bin_pass2(crpt, mw, rs, soff, d_counters(h, 0), d_bins(h), h->stream) != cudaSuccess)
+        if (note(launch_bin_pass2(crpt, mw, rs, soff, d_counters(h, 0), d_bins(h), h->stream)) != cudaSuccess)
             return fail(SPGEMM_ERR_CUDA);
         time_end(h, kSlotSymPass2, h->stream);
     }
@@ -768,10 +836,11 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     rn.nb = h->cfg.num_nbins;
     for (int j = 0; j < rn.nb; ++j) rn.r[j] = h->cfg.num_range[j];
     time_begin(h, kSlotNumPass1, h->stream);
-    if (launch_bin_pass1(crpt, mw, rn, op, d_counters(h, 1), d_tiles(h), h->stream) != cudaSuccess)
+    if (note(launch_bin_pass1(crpt, mw, rn, op, d_counters(h, 1), d_tiles(h), h->stream)) != cudaSuccess)
         return fail(SPGEMM_ERR_CUDA);
     time_end(h, kSlotNumPass1, h->stream);
     if ((rc = read_counters(h))) return fail(rc);
+    h->b_unsorted = (h->h_cnt[1].flags & 1ull) != 0;
     h->stats[2] = static_cast<int64_t>(h->h_cnt[1].total);
     h->stats[3] = static_cast<int64_t>(h->h_cnt[1].max_size);
     for (int j = 0; j < SPGEMM_MAX_BINS; ++j)
@@ -831,6 +900,10 @@ int spgemm_numeric(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in
         acc += h->num_size[j];
         nonempty += h->num_size[j] > 0;
     }
+    // windowed pass 2 for the bitmap bin when every row of B is sorted
+    RunPlan rp = h->rplan;
+    if (h->b_unsorted || !num_kernel(h->cfg.num_kernel[nb - 1]).bitmap || h->num_size[nb - 1] <= 0)
+        rp = RunPlan{};
     const bool nid = nonempty <= 1;
     Ranges rn{};
     rn.nb = nb;
@@ -847,12 +920,12 @@ int spgemm_numeric(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in
     };
     if (!nid) {
         time_begin(h, kSlotNumPass2, h->stream);
-        if (launch_bin_pass2(crpt, h->mw, rn, off, d_counters(h, 1), d_bins(h), h->stream) != cudaSuccess)
+        if (note(launch_bin_pass2(crpt, h->mw, rn, off, d_counters(h, 1), d_bins(h), h->stream)) != cudaSuccess)
             return fail(SPGEMM_ERR_CUDA);
         time_end(h, kSlotNumPass2, h->stream);
     }
     time_begin(h, kSlotScan, h->stream);
-    if (launch_scan(crpt, h->mw, d_tiles(h), h->stream) != cudaSuccess) return fail(SPGEMM_ERR_CUDA);
+    if (note(launch_scan(crpt, h->mw, d_tiles(h), h->stream)) != cudaSuccess) return fail(SPGEMM_ERR_CUDA);
     time_end(h, kSlotScan, h->stream);
     // C.col / C.val allocated while the binning and scan kernels run (Sec. 5.4)
     if (!given) {
@@ -860,7 +933,21 @@ int spgemm_numeric(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in
         cval = static_cast<double *>(dev_alloc(h, sizeof(double) * (size_t)h->nnz));
         if (!ccol || !cval) return fail(SPGEMM_ERR_OOM);
     }
-    if ((rc = run_bins(h, 1, op, h->num_size, off, nid, crpt, ccol, cval))) return fail(rc);
+    // run boundaries of B's rows at the column sub-ranges, for the windowed pass 2
+    int32_t *bs = nullptr;
+    if (rp.lists > 0) {
+        bs = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * (size_t)B->rows * (size_t)(rp.G + 1)));
+        if (!bs) return fail(SPGEMM_ERR_OOM);
+        if (note(launch_bsplit(op, B->rows, B->nnz, rp.gshift, rp.G, bs, h->sm_count * 4, h->stream)) !=
+            cudaSuccess) {
+            dev_free(h, bs);
+            return fail(SPGEMM_ERR_CUDA);
+        }
+        rp.bs = bs;
+    }
+    rc = run_bins(h, 1, op, h->num_size, off, nid, crpt, ccol, cval, &rp);
+    dev_free(h, bs);
+    if (rc) return fail(rc);
     C->rows = h->mw;
     C->cols = h->ncols;
     C->nnz = h->nnz;

@@ -230,6 +230,52 @@ __device__ __forceinline__ long long block_excl_scan_ll(long long x, long long &
     }
 }
 
+// L2 residency of a C.val segment that float64 reductions go into: its
+// zeroing stores and the reductions carry an evict_last policy, so the B rows
+// streaming through L2 evict other lines first; once the row is done its
+// lines drop back to normal priority (applypriority, one 128-byte line).
+__device__ __forceinline__ unsigned long long l2_evict_last_policy() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void st_keep(double *p, double v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void red_add_keep(double *p, double v, unsigned long long pol) {
+    asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void l2_priority_normal(const void *p) {
+    asm volatile("applypriority.global.L2::evict_normal [%0], 128;" ::"l"(p) : "memory");
+}
+
+// Exclusive scan of one unsigned per thread over a block of BLOCK threads.
+template <int BLOCK>
+__device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned &total, unsigned *sw) {
+    const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    unsigned inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= static_cast<unsigned>(o)) inc += y;
+    }
+    __syncthreads();
+    if (lane == 31) sw[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const unsigned t = lane < (BLOCK >> 5) ? sw[lane] : 0u;
+        unsigned ti = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= static_cast<unsigned>(o)) ti += y;
+        }
+        if (lane < (BLOCK >> 5)) sw[lane] = ti - t;
+        if (lane == 31) sw[32] = ti;
+    }
+    __syncthreads();
+    total = sw[32];
+    return sw[w] + inc - x;
+}
+
 // Calls f(key, a_value, b_value) for every product of the row [p0, p1) of A
 // (a_value and b_value only when NEED_VAL). Every thread of the block must
 // call it (it synchronises the block). A lane's products of one piece (at

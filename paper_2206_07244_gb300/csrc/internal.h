@@ -28,6 +28,12 @@ struct BinWork {
     int lanes;            // threads per B row, 0 = per-row automatic
     int unroll;           // bitmap kernels: products in flight per lane (4 or 8; 0 = 4)
     int *err;             // device error word
+    // numeric bitmap kernel, pass 2 by column windows (B rows sorted)
+    const int32_t *bs;    // run boundaries of B rows at the sub-ranges (G + 1 per row), or nullptr
+    int G, gshift;        // sub-ranges of 2^gshift columns
+    int wlists;           // rows with more A entries use the whole-row pass 2
+    int wentries;         // C entries per window, about
+    int head;             // shared bytes before the bitmap (set by launch_num)
     // one-phase (learned sizing) numeric kernels only
     int32_t *tcol;        // temporary rows: bin-local row r of this bin at
     double *tval;         //   tcol/tval + tbase + r * tcap
@@ -52,7 +58,14 @@ struct Counters {
     unsigned long long bin_nnza[kMaxBins];  // pass 1: A entries of the bin's rows
     unsigned long long max_size;
     unsigned long long total;
+    unsigned long long flags;         // bit 0: some row of B has decreasing columns
 };
+
+// Windowed pass 2 of the numeric bitmap kernel: at most kWinMaxLists A
+// entries per row, at most kRunMaxSub column sub-ranges.
+constexpr int kWinMaxLists = 1024;
+constexpr int kRunMaxSub = 64;
+constexpr int kRunDefaultEntries = 12288;
 
 // Kernel table entry (host side).
 struct KernelDesc {
@@ -72,6 +85,10 @@ cudaError_t launch_bin_pass1(const int64_t *sizes, int64_t n, const Ranges &rg,
 cudaError_t launch_bin_pass2(const int64_t *sizes, int64_t n, const Ranges &rg,
                              const long long *offsets, Counters *cnt, int32_t *bins,
                              cudaStream_t s);
+// Sets bit 0 of cnt->flags when some row of B has a column smaller than the
+// one before it.
+cudaError_t launch_sorted_check(const Operands &op, int64_t brows, int64_t bnnz, Counters *cnt,
+                                int grid, cudaStream_t s);
 // In-place exclusive scan of crpt[0..n) using per-tile sums from pass 1;
 // writes crpt[n] = total. tile_sums needs room for ntiles + 1 entries.
 cudaError_t launch_scan(int64_t *crpt, int64_t n, long long *tile_sums, cudaStream_t s);
@@ -91,6 +108,15 @@ cudaError_t launch_num(int id, const Operands &op, const BinWork &w, size_t smem
                        cudaStream_t s);
 // one-phase numeric kernel `id` (a hash kernel of the numeric table)
 cudaError_t launch_num_onephase(int id, const Operands &op, const BinWork &w, cudaStream_t s);
+
+// --- runs.cu -------------------------------------------------------------------
+// Run boundaries of B rows at column sub-ranges of 2^gshift columns
+// (G + 1 int32 per row of B: offset of the first entry of each sub-range).
+cudaError_t launch_bsplit(const Operands &op, int64_t brows, int64_t bnnz, int gshift, int G,
+                          int32_t *bs, int grid, cudaStream_t s);
+// numeric.cu: shared bytes before the bitmap of num_bitmap_kernel (walk
+// scratch, or the run metadata of a windowed pass 2).
+size_t num_bitmap_head_bytes(bool runs);
 
 // --- batch.cu ------------------------------------------------------------------
 struct BatchProb {

@@ -200,31 +200,72 @@ num_hash_kernel(Operands op, BinWork w) {
     }
 }
 
-// Exclusive scan of one unsigned per thread over a block of BLOCK threads.
-template <int BLOCK>
-__device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned &total, unsigned *sw) {
-    const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-    unsigned inc = x;
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= static_cast<unsigned>(o)) inc += y;
-    }
-    __syncthreads();
-    if (lane == 31) sw[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        const unsigned t = lane < (BLOCK >> 5) ? sw[lane] : 0u;
-        unsigned ti = t;
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, ti, o);
-            if (lane >= static_cast<unsigned>(o)) ti += y;
+// Pass 2 by column windows (B rows sorted, run boundaries from bsplit): the
+// row's products whose columns fall in sub-ranges [g, g2) of the column
+// space are, per A entry, one run of its B row; the runs of a window are
+// concatenated into one flat index space that the block's warps split into
+// equal contiguous ranges. Windows hold about w.wentries entries of C, so
+// the C.val lines that the float64 reductions of a window hit stay in L2.
+struct RunMeta {
+    long long q0[kWinMaxLists];      // first B entry of each A entry's B row
+    double aval[kWinMaxLists];       // A values of the row
+    int32_t ks[kWinMaxLists];        // B row of each A entry
+    int32_t rs[kWinMaxLists];        // run start (offset in the B row) of the current window
+    long long lp[kWinMaxLists + 1];  // exclusive prefix of the run lengths
+    long long red[33];               // block scan scratch
+    int g2;                          // end sub-range of the current window
+};
+
+
+size_t num_bitmap_head_bytes(bool runs) {
+    const size_t a = sizeof(WalkScratch), b = sizeof(RunMeta);
+    const size_t h = runs && b > a ? b : a;
+    return (h + 15) & ~static_cast<size_t>(15);
+}
+
+// Calls f(col, a_value, b_value) for every product of the current window's
+// runs (rm->lp holds their exclusive prefix, `total` the sum). A lane loads
+// UNROLL products before using any.
+template <int BLOCK, int UNROLL, typename F>
+__device__ __forceinline__ void run_walk(const Operands &op, const RunMeta *rm, int nl, long long total,
+                                         F &&f) {
+    constexpr int kWarps = BLOCK / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long per = (total + kWarps - 1) / kWarps;
+    const long long f0 = per * warp;
+    const long long f1 = f0 + per < total ? f0 + per : total;
+    if (f0 >= f1) return;
+    int t = 0;
+    {   // run of the lane's first index: last t with lp[t] <= f0 + lane
+        const long long first = f0 + lane;
+        int lo = 0, hi = nl;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (rm->lp[mid] <= first) lo = mid; else hi = mid;
         }
-        if (lane < (BLOCK >> 5)) sw[lane] = ti - t;
-        if (lane == 31) sw[32] = ti;
+        t = lo;
     }
-    __syncthreads();
-    total = sw[32];
-    return sw[w] + inc - x;
+    for (long long base = f0; base < f1; base += 32 * UNROLL) {
+        int c[UNROLL], tt[UNROLL];
+        double b[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const long long idx = base + u * 32 + lane;
+            c[u] = -1;
+            tt[u] = t;
+            b[u] = 0.0;
+            if (idx < f1) {
+                while (rm->lp[t + 1] <= idx) ++t;   // runs are visited in order
+                tt[u] = t;
+                const long long q = rm->q0[t] + rm->rs[t] + (idx - rm->lp[t]);
+                c[u] = __ldg(op.bcol + q);
+                b[u] = __ldg(op.bval + q);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u)
+            if (c[u] >= 0) f(c[u], rm->aval[tt[u]], b[u]);
+    }
 }
 
 template <int BLOCK, int ITERS>
@@ -232,8 +273,11 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 1024 ? 1 : 1536 / BLOCK)
 num_bitmap_kernel(Operands op, BinWork w, int words) {
     constexpr int kBmBlock = BLOCK;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // the head holds the walk scratch of pass 1, then the run metadata of a
+    // windowed pass 2
     WalkScratch *sc = reinterpret_cast<WalkScratch *>(smem_raw);
-    unsigned long long *bm = reinterpret_cast<unsigned long long *>(smem_raw + sizeof(WalkScratch));
+    RunMeta *rm = reinterpret_cast<RunMeta *>(smem_raw);
+    unsigned long long *bm = reinterpret_cast<unsigned long long *>(smem_raw + w.head);
     unsigned *bm32 = reinterpret_cast<unsigned *>(bm);   // same words, 32-bit halves
     unsigned *pre = reinterpret_cast<unsigned *>(bm + words);
     __shared__ long long red64[32];
@@ -296,7 +340,72 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
                     ccol[pos++] = colbase + b;
                 }
             }
-            for (int64_t t = threadIdx.x; t < cnt; t += kBmBlock) cval[t] = 0.0;
+            const unsigned long long pol = l2_evict_last_policy();
+            const int nl = static_cast<int>(p1 - p0 < INT32_MAX ? p1 - p0 : INT32_MAX);
+            // one thread per A entry: the row's A entries must fit the block
+            if (w.bs && c0 == 0 && span >= op.ncols && nl <= w.wlists && nl <= kBmBlock) {
+                // pass 2 by column windows of about w.wentries entries
+                bool bad = false;
+                if (threadIdx.x < nl) {
+                    const int k = __ldg(op.acol + p0 + threadIdx.x);
+                    rm->ks[threadIdx.x] = k;
+                    rm->q0[threadIdx.x] = ld_rpt(op.brpt, op.b64, k);
+                    rm->aval[threadIdx.x] = __ldg(op.aval + p0 + threadIdx.x);
+                    rm->rs[threadIdx.x] = 0;
+                }
+                // rank of the first column of sub-range g (sub-ranges start on word boundaries)
+                auto bnd_rank = [&](int g) -> unsigned {
+                    const int64_t cb = static_cast<int64_t>(g) << w.gshift;
+                    return cb >= op.ncols ? static_cast<unsigned>(cnt) : pre[cb >> 6];
+                };
+                for (int g = 0; g < w.G;) {
+                    if (threadIdx.x == 0) {
+                        const unsigned r0 = bnd_rank(g);
+                        int g2 = g + 1;
+                        while (g2 < w.G && bnd_rank(g2 + 1) - r0 <= static_cast<unsigned>(w.wentries)) ++g2;
+                        rm->g2 = g2;
+                    }
+                    __syncthreads();
+                    const int g2 = rm->g2;
+                    const unsigned r_lo = bnd_rank(g), r_hi = bnd_rank(g2);
+                    long long len = 0;
+                    int re = 0;
+                    if (threadIdx.x < nl) {
+                        re = __ldg(w.bs + static_cast<int64_t>(rm->ks[threadIdx.x]) * (w.G + 1) + g2);
+                        len = re - rm->rs[threadIdx.x];
+                    }
+                    for (unsigned t = r_lo + threadIdx.x; t < r_hi; t += kBmBlock) st_keep(cval + t, 0.0, pol);
+                    long long total;
+                    const long long ex = block_excl_scan_ll<kBmBlock>(len, total, rm->red);
+                    if (threadIdx.x < nl) rm->lp[threadIdx.x] = ex;
+                    if (threadIdx.x == 0) rm->lp[nl] = total;
+                    __syncthreads();
+                    if (total > 0)
+                        run_walk<kBmBlock, kBmBlock == 1024 ? 8 : 4>(op, rm, nl, total,
+                                                                      [&](int key, double a, double b) {
+                            const unsigned rel = static_cast<unsigned>(key - c0i);
+                            const unsigned wi = rel >> 6, bi = rel & 63u;
+                            const unsigned rank = rel < span32 ? pre[wi] +
+                                static_cast<unsigned>(__popcll(bm[wi] << (63u - bi))) - 1u : 0u;
+                            if (rel < span32 && rank >= r_lo && rank < r_hi) red_add_keep(cval + rank, a * b, pol);
+                            else bad = true;
+                        });
+                    __syncthreads();
+                    const uintptr_t l0 = reinterpret_cast<uintptr_t>(cval + r_lo) & ~static_cast<uintptr_t>(127);
+                    const uintptr_t l1 = reinterpret_cast<uintptr_t>(cval + r_hi);
+                    for (uintptr_t l = l0 + 128 * static_cast<uintptr_t>(threadIdx.x); l < l1;
+                         l += 128 * static_cast<uintptr_t>(kBmBlock))
+                        l2_priority_normal(reinterpret_cast<const void *>(l));
+                    if (threadIdx.x < nl) rm->rs[threadIdx.x] = re;
+                    g = g2;
+                    __syncthreads();
+                }
+                if (bad) set_error(w.err, DERR_WINDOW);
+                done += cnt;
+                __syncthreads();
+                continue;
+            }
+            for (int64_t t = threadIdx.x; t < cnt; t += kBmBlock) st_keep(cval + t, 0.0, pol);
             __syncthreads();
             // pass 2: each product lands on its column's rank
             block_row_walk<kBmBlock, true, ITERS>(op, p0, p1, S, sc, [&](int key, double a, double b) {
@@ -307,9 +416,16 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
                     // top, counted, minus itself = columns before it in the word
                     const unsigned rank = pre[wi] +
                         static_cast<unsigned>(__popcll(bm[wi] << (63u - bi))) - 1u;
-                    atomicAdd(cval + rank, a * b);
+                    red_add_keep(cval + rank, a * b, pol);
                 }
             });
+            __syncthreads();
+            // back to normal priority: every 128-byte line the segment touches
+            const uintptr_t l0 = reinterpret_cast<uintptr_t>(cval) & ~static_cast<uintptr_t>(127);
+            const uintptr_t l1 = reinterpret_cast<uintptr_t>(cval + cnt);
+            for (uintptr_t l = l0 + 128 * static_cast<uintptr_t>(threadIdx.x); l < l1;
+                 l += 128 * static_cast<uintptr_t>(kBmBlock))
+                l2_priority_normal(reinterpret_cast<const void *>(l));
         }
         done += cnt;
         __syncthreads();
@@ -462,9 +578,12 @@ cudaError_t launch_num(int id, const Operands &op, const BinWork &w, size_t smem
         g_num[id].fn<<<static_cast<unsigned>(grid), d.block, d.smem, s>>>(op, w);
     } else {
         const int words = static_cast<int>(smem_bitmap / 12);
-        const size_t smem = smem_bitmap + sizeof(WalkScratch);
+        BinWork wk = w;
+        wk.head = static_cast<int>(num_bitmap_head_bytes(w.bs != nullptr));
+        if (!w.bs) wk.wlists = 0;
+        const size_t smem = smem_bitmap + static_cast<size_t>(wk.head);
         const auto &v = g_num_bm[pick_bitmap_variant(smem, w.unroll)];
-        v.fn<<<static_cast<unsigned>(w.cnt), v.block, smem, s>>>(op, w, words);
+        v.fn<<<static_cast<unsigned>(w.cnt), v.block, smem, s>>>(op, wk, words);
     }
     return cudaGetLastError();
 }

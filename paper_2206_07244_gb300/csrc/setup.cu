@@ -203,6 +203,43 @@ cudaError_t launch_bin_pass2(const int64_t *sizes, int64_t n, const Ranges &rg,
 }
 
 // ---------------------------------------------------------------------------
+// Is every row of B sorted by column? (The column-window numeric kernel walks
+// B rows with cursors and needs non-decreasing columns.) Work is split over
+// B's non-zeros; each thread checks the pairs (e, e + 1) of its entries that
+// lie in one row.
+constexpr int kSortItems = 8;
+
+__global__ void __launch_bounds__(kBinBlock)
+sorted_check_kernel(Operands op, int64_t brows, int64_t bnnz, Counters *cnt) {
+    const int64_t tile = static_cast<int64_t>(blockDim.x) * kSortItems;
+    bool bad = false;
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * tile; base < bnnz - 1;
+         base += static_cast<int64_t>(gridDim.x) * tile) {
+        const int64_t e0 = base + static_cast<int64_t>(threadIdx.x) * kSortItems;
+        if (e0 >= bnnz - 1) continue;
+        int64_t row = upper_bound_rpt(op.brpt, op.b64, 0, brows, e0);
+        int64_t next = ld_rpt(op.brpt, op.b64, row + 1);
+        for (int j = 0; j < kSortItems; ++j) {
+            const int64_t e = e0 + j;
+            if (e >= bnnz - 1) break;
+            while (e >= next) {
+                row = upper_bound_rpt(op.brpt, op.b64, row + 1, brows, e);
+                next = ld_rpt(op.brpt, op.b64, row + 1);
+            }
+            if (e + 1 < next && __ldg(op.bcol + e + 1) < __ldg(op.bcol + e)) bad = true;
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31u) == 0) atomicOr(&cnt->flags, 1ull);
+}
+
+cudaError_t launch_sorted_check(const Operands &op, int64_t brows, int64_t bnnz, Counters *cnt,
+                                int grid, cudaStream_t s) {
+    if (bnnz <= 1 || brows <= 0) return cudaSuccess;
+    sorted_check_kernel<<<grid, kBinBlock, 0, s>>>(op, brows, bnnz, cnt);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Exclusive scan of the row sizes into C.rpt, in place (Sec. 5.3). Tile t
 // covers rows [t*kBinTile, (t+1)*kBinTile), the same tiles whose sums
 // bin_pass1_kernel stored.
