@@ -5,6 +5,7 @@ through the host-buffer C ABI call.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                     [--impl ours|reference] [--no-e2e] [--no-cpu-baseline]
+                    [--legs all|none|learned|batched]
 
 Default workload: R-MAT n = 2^20, average degree 16 (a=.57, b=c=.19), seed 1,
 float64 values uniform in [-1, 1] (about 2.09e10 products, 9.7e9 entries in C,
@@ -396,11 +397,12 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="also tune the bin configuration and time plain vs tuned")
     ap.add_argument("--save-config", default=None)
-    ap.add_argument("--learned", action="store_true",
-                    help="also compare learned sizing with the plain path (trained weights)")
-    ap.add_argument("--batched", action="store_true",
-                    help="also run the 512 Galerkin products plain vs batched (autotuned)")
+    ap.add_argument("--legs", default="all", choices=["all", "none", "learned", "batched"],
+                    help="extra comparisons after the main line: learned sizing vs plain "
+                         "(trained weights) and 512 Galerkin products plain vs batched")
     args = ap.parse_args()
+    args.learned = args.legs in ("all", "learned")
+    args.batched = args.legs in ("all", "batched")
     if args.warmup < 3 and args.impl == "ours" and not os.environ.get("BENCH_ALLOW_SHORT"):
         args.warmup = 3
     if args.impl == "reference":
@@ -569,6 +571,11 @@ def main():
         del R
         S = W.stencil27(128, seed=3)
         learned_legs.append(learned_eval("27-point stencil 128^3", S, 0, S.rows))
+        del S
+        D = W.block_diagonal(1 << 20, 1024, 24.0, seed=7)
+        learned_legs.append(learned_eval("random block-diagonal n=2^20, 1024 blocks, mean degree 24, "
+                                         "seed 7 (the training families, unseen size and seed)",
+                                         D, 0, D.rows))
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "GFLOPS", "n_gpus": ws,

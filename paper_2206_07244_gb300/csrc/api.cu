@@ -471,7 +471,8 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
     const int nb = h->cfg.num_nbins;
     const int last = nb - 1;   // the numeric bitmap bin: exact path
     const int64_t cap = nb >= 2 ? h->cfg.num_range[nb - 2] : 0;
-    long long *fnp = reinterpret_cast<long long *>(L.fws);
+    // the features kernel also leaves n_prod of every row in C.rpt (step 1)
+    long long *fnp = reinterpret_cast<long long *>(crpt);
     unsigned *fmx = reinterpret_cast<unsigned *>(L.fws + sizeof(long long) * (size_t)mw);
     unsigned *fmn = fmx + mw;
     time_begin(h, kSlotFeatures, s);
@@ -776,10 +777,6 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
         note(cudaMemsetAsync(crpt, 0, sizeof(int64_t) * (size_t)(mw + 1), h->stream)) != cudaSuccess)
         return fail(SPGEMM_ERR_CUDA);
     const Operands op = make_operands(A, B, row_begin, mw);
-    // step 1: n_prod per row into C.rpt
-    time_begin(h, kSlotNprod, h->stream);
-    if (note(launch_nprod(op, crpt, h->sm_count * 8, h->stream)) != cudaSuccess) return fail(SPGEMM_ERR_CUDA);
-    time_end(h, kSlotNprod, h->stream);
     if (h->mode == SPGEMM_MODE_LEARNED) {
         // the one-phase kernels multiply during this call: they read values
         if ((A->nnz > 0 && !A->val) || (B->nnz > 0 && !B->val)) return fail(SPGEMM_ERR_INVALID);
@@ -804,6 +801,10 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
         return SPGEMM_OK;
     }
     // rows of B must be sorted for the windowed pass 2 of the numeric bitmap kernel
+    // step 1: n_prod per row into C.rpt
+    time_begin(h, kSlotNprod, h->stream);
+    if (note(launch_nprod(op, crpt, h->sm_count * 8, h->stream)) != cudaSuccess) return fail(SPGEMM_ERR_CUDA);
+    time_end(h, kSlotNprod, h->stream);
     h->rplan = run_plan(h->cfg, h->smem_dyn_max, B->cols);
     if (h->rplan.lists > 0 &&
         note(launch_sorted_check(op, B->rows, B->nnz, d_counters(h, 1), h->sm_count * 4, h->stream)) !=

@@ -113,21 +113,43 @@ static_assert(kParams == 4673, "parameter count");
 
 int mlp_param_count() { return kParams; }
 
+// One row through the network. Weights are read from shared memory four at
+// a time (16-byte broadcast loads: every thread of a warp reads the same
+// address); each hidden unit sums its inputs in ascending order.
 __device__ __forceinline__ float mlp_row(const float *w, const float *x) {
     float h1[kH];
 #pragma unroll
-    for (int a = 0; a < kH; ++a) {
-        float z = w[kOffB1 + a];
+    for (int a = 0; a < kH; a += 4) {
+        float4 z = *reinterpret_cast<const float4 *>(w + kOffB1 + a);
 #pragma unroll
-        for (int f = 0; f < kIn; ++f) z = fmaf(x[f], w[kOffW1 + f * kH + a], z);
-        h1[a] = fmaxf(z, 0.f);
+        for (int f = 0; f < kIn; ++f) {
+            const float4 wv = *reinterpret_cast<const float4 *>(w + kOffW1 + f * kH + a);
+            z.x = fmaf(x[f], wv.x, z.x);
+            z.y = fmaf(x[f], wv.y, z.y);
+            z.z = fmaf(x[f], wv.z, z.z);
+            z.w = fmaf(x[f], wv.w, z.w);
+        }
+        h1[a] = fmaxf(z.x, 0.f);
+        h1[a + 1] = fmaxf(z.y, 0.f);
+        h1[a + 2] = fmaxf(z.z, 0.f);
+        h1[a + 3] = fmaxf(z.w, 0.f);
     }
     float y = w[kOffB3];
-    for (int j = 0; j < kH; ++j) {
-        float z = w[kOffB2 + j];
+    for (int j = 0; j < kH; j += 4) {
+        float4 z = *reinterpret_cast<const float4 *>(w + kOffB2 + j);
 #pragma unroll
-        for (int a = 0; a < kH; ++a) z = fmaf(h1[a], w[kOffW2 + a * kH + j], z);
-        y = fmaf(fmaxf(z, 0.f), w[kOffW3 + j], y);
+        for (int a = 0; a < kH; ++a) {
+            const float4 wv = *reinterpret_cast<const float4 *>(w + kOffW2 + a * kH + j);
+            z.x = fmaf(h1[a], wv.x, z.x);
+            z.y = fmaf(h1[a], wv.y, z.y);
+            z.z = fmaf(h1[a], wv.z, z.z);
+            z.w = fmaf(h1[a], wv.w, z.w);
+        }
+        const float4 w3 = *reinterpret_cast<const float4 *>(w + kOffW3 + j);
+        y = fmaf(fmaxf(z.x, 0.f), w3.x, y);
+        y = fmaf(fmaxf(z.y, 0.f), w3.y, y);
+        y = fmaf(fmaxf(z.z, 0.f), w3.z, y);
+        y = fmaf(fmaxf(z.w, 0.f), w3.w, y);
     }
     return y;
 }
@@ -137,7 +159,7 @@ __device__ __forceinline__ float mlp_row(const float *w, const float *x) {
 __global__ void __launch_bounds__(256)
 mlp_forward_kernel(const float *theta, const float *X, int64_t n, float *y, long long *sizes,
                    float margin, long long cap) {
-    __shared__ float w[kParams];
+    __shared__ __align__(16) float w[kParams + 3];
     for (int i = threadIdx.x; i < kParams; i += blockDim.x) w[i] = theta[i];
     __syncthreads();
     const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;

@@ -3,6 +3,9 @@ float64): features, forward pass, gradients, Adam; and the learned-mode
 product, which must equal the oracle's C whatever the predictor says
 (trained, predicting 1 for every row, or predicting more than any table)."""
 
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -181,3 +184,45 @@ def test_learned_symbolic_without_values_is_rejected(trained):
                                         ctypes.byref(nnz))
         assert rc == -1
         h.status()
+
+
+def _median_ms(h, dA, reps=5):
+    ts = []
+    for _ in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        C = h.multiply(dA, dA)
+        e1.record()
+        e1.synchronize()
+        del C
+        ts.append(e0.elapsed_time(e1))
+    h.status()
+    return float(np.median(ts[1:]))
+
+
+def test_trained_network_gain():
+    # The committed network against the two sizings without it: the exact
+    # symbolic pass (plain mode) and the n_prod upper bound (a network that
+    # over-predicts every row). On rows that fit the hash bins (a 27-point
+    # stencil, 64^3) the network must beat the upper bound by 10%; the ratio
+    # to the plain path is reported, not asserted.
+    if not os.path.exists(learned.WEIGHTS):
+        pytest.skip("no trained weights")
+    theta = np.load(learned.WEIGHTS)
+    margin = json.load(open(learned.MANIFEST))["margin"]
+    A = W.stencil27(64, seed=77)
+    dA = dev(A)
+    with ops.Handle() as h:
+        t_plain = _median_ms(h, dA)
+        h.set_predictor(theta, margin)
+        h.set_mode("learned")
+        t_learned = _median_ms(h, dA)
+        st = h.learned_stats()
+        big = np.zeros_like(theta)
+        big[-1] = 30.0
+        h.set_predictor(big, 0.0)
+        t_bound = _median_ms(h, dA)
+    print(f"plain {t_plain:.3f} ms, learned {t_learned:.3f} ms, n_prod bound {t_bound:.3f} ms, "
+          f"learned/plain speedup {t_plain / t_learned:.3f}, stats {st}")
+    assert st["one_phase_rows"] > 0.9 * A.rows
+    assert t_learned < 0.9 * t_bound
