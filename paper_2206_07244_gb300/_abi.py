@@ -50,7 +50,8 @@ class CsrOut(ctypes.Structure):
 
 class BatchOptions(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
-                ("spin_limit", ctypes.c_int64)]
+                ("spin_limit", ctypes.c_int64), ("no_tiny", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Config(ctypes.Structure):

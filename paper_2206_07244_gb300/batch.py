@@ -13,7 +13,7 @@ class Batch:
     product j (b_from[i] = j). Inputs must stay alive while the batch does."""
 
     def __init__(self, handle: Handle, As, Bs, b_from=None, variant: int = -1, tile_rows: int = 0,
-                 spin_limit: int = 0):
+                 spin_limit: int = 0, tiny: bool = True):
         import torch
         n = len(As)
         self._h = handle
@@ -26,7 +26,7 @@ class Batch:
                 bb[i] = _csr_in(Bs[i])
         dep = (ctypes.c_int32 * max(n, 1))(*([(-1 if b_from is None else int(b_from[i])) for i in range(n)]
                                               or [0]))
-        opt = _abi.BatchOptions(variant, tile_rows, spin_limit)
+        opt = _abi.BatchOptions(variant, tile_rows, spin_limit, 0 if tiny else 1, 0)
         self._b = ctypes.c_void_p()
         lib = _abi.lib()
         self._lib = lib

@@ -1351,7 +1351,7 @@ int spgemm_batch_create(spgemm_batch **out, spgemm_handle *h, int n, const spgem
     // whose B is an earlier C, the n_prod of that C's rows bounds their size,
     // so a pseudo row pointer built from those bounds gives a bound here
     std::vector<std::vector<int64_t>> bound(n);
-    std::vector<int64_t> cap(n, 0);
+    std::vector<int64_t> cap(n, 0), pmax(n, 0);
     int64_t maxrow = 0;
     int64_t *d_b = nullptr, *d_rp = nullptr;
     size_t d_b_n = 0, d_rp_n = 0;
@@ -1391,6 +1391,7 @@ int spgemm_batch_create(spgemm_batch **out, spgemm_handle *h, int n, const spgem
         CK(cudaStreamSynchronize(h->stream));
         for (int64_t v : bound[i]) {
             cap[i] += v;
+            pmax[i] = std::max(pmax[i], v);
             maxrow = std::max(maxrow, v);
         }
     }
@@ -1409,7 +1410,7 @@ int spgemm_batch_create(spgemm_batch **out, spgemm_handle *h, int n, const spgem
     }
     if (b->variant < 0) return fail(SPGEMM_ERR_INVALID);   // rows too large to batch
     const int rg = 256 / batch_variant_lanes(b->variant);
-    b->tile_rows = (opt && opt->tile_rows > 0) ? opt->tile_rows : rg * 4;
+    b->tile_rows = (opt && opt->tile_rows > 0) ? opt->tile_rows : rg * 32;
     if (b->tile_rows % rg) b->tile_rows += rg - b->tile_rows % rg;
     b->spin_limit = (opt && opt->spin_limit > 0) ? opt->spin_limit : (1LL << 22);
     // arena: per product C.rpt (M+1 int64), C.col and C.val with room for the bound
@@ -1439,6 +1440,8 @@ int spgemm_batch_create(spgemm_batch **out, spgemm_handle *h, int n, const spgem
         P.ccap = cap[i];
         P.ntiles = static_cast<int32_t>((P.M + b->tile_rows - 1) / b->tile_rows);
         P.dep = dep;
+        P.tiny = pmax[i] <= kBatchTiny && !(opt && opt->no_tiny) ? 1 : 0;
+        P.pad = 0;
         if (dep < 0) {
             P.brpt = B[i].rpt; P.b64 = B[i].rpt_is_i64 ? 1 : 0; P.bcol = B[i].col; P.bval = B[i].val;
         } else {

@@ -101,11 +101,69 @@ __device__ __forceinline__ bool batch_row(const BatchProb &P, int64_t row, int *
     return ok;
 }
 
+// Rows of a product with at most kBatchTiny products each (P.tiny): one
+// thread per row keeps the row's distinct columns sorted in kBatchTiny
+// shared slots of its own (slot j of thread t at j * kBatchBlock + t, so the
+// threads of a warp hit distinct banks), adding equal columns in product
+// order; the row is then stored as it stands, without condense or sort.
+template <bool NUMERIC, bool COHERENT>
+__device__ __forceinline__ bool tiny_rows(const BatchProb &P, int64_t r0, int64_t r1, int *keys,
+                                          double *vals) {
+    bool ok = true;
+    const int t = threadIdx.x;
+    for (int64_t row = r0 + t; row < r1; row += kBatchBlock) {
+        int n = 0;
+        const int64_t p0 = ld_rpt(P.arpt, P.a64, row), p1 = ld_rpt(P.arpt, P.a64, row + 1);
+        for (int64_t p = p0; p < p1; ++p) {
+            const int k = __ldg(P.acol + p);
+            const double a = NUMERIC ? __ldg(P.aval + p) : 0.0;
+            const int64_t q1 = bload_rpt<COHERENT>(P.brpt, P.b64, k + 1);
+            for (int64_t q = bload_rpt<COHERENT>(P.brpt, P.b64, k); q < q1; ++q) {
+                const int key = bload_col<COHERENT>(P.bcol, q);
+                const double v = NUMERIC ? a * bload_val<COHERENT>(P.bval, q) : 0.0;
+                int pos = 0;
+                while (pos < n && keys[pos * kBatchBlock + t] < key) ++pos;
+                if (pos < n && keys[pos * kBatchBlock + t] == key) {
+                    if (NUMERIC) vals[pos * kBatchBlock + t] += v;
+                    continue;
+                }
+                if (n == kBatchTiny) {   // more than the bound: cannot happen
+                    ok = false;
+                    continue;
+                }
+                for (int m = n; m > pos; --m) {
+                    keys[m * kBatchBlock + t] = keys[(m - 1) * kBatchBlock + t];
+                    if (NUMERIC) vals[m * kBatchBlock + t] = vals[(m - 1) * kBatchBlock + t];
+                }
+                keys[pos * kBatchBlock + t] = key;
+                if (NUMERIC) vals[pos * kBatchBlock + t] = v;
+                ++n;
+            }
+        }
+        if (!NUMERIC) {
+            P.crpt[row] = n;
+        } else {
+            const int64_t base = __ldcg(reinterpret_cast<const long long *>(P.crpt) + row);
+            const int64_t want = __ldcg(reinterpret_cast<const long long *>(P.crpt) + row + 1) - base;
+            if (want != n || base + n > P.ccap) {
+                ok = false;
+            } else {
+                for (int m = 0; m < n; ++m) {
+                    P.ccol[base + m] = keys[m * kBatchBlock + t];
+                    P.cval[base + m] = vals[m * kBatchBlock + t];
+                }
+            }
+        }
+    }
+    return ok;
+}
+
 template <int G, int T>
 __global__ void __launch_bounds__(kBatchBlock)
 batch_kernel(const BatchProb *probs, const BatchItem *items, int nitems, BatchState *st,
              int *done_s, int *xflag, int *done_n, int tile_rows, long long spin_limit) {
     constexpr int RG = kBatchBlock / G;
+    static_assert(RG * T >= kBatchTiny * kBatchBlock, "tiny rows reuse the tables");
     __shared__ int keys_all[RG * T];
     __shared__ double vals_all[RG * T];
     __shared__ int red32[33];
@@ -164,7 +222,15 @@ batch_kernel(const BatchProb *probs, const BatchItem *items, int nitems, BatchSt
         const int64_t r1 = r0 + tile_rows < P.M ? r0 + tile_rows : P.M;
         const bool coherent = P.dep >= 0;
         bool ok_all = true;
-        for (int64_t rb = r0; rb < r1; rb += RG) {
+        if (P.tiny) {
+            if (I.type == 0)
+                ok_all = coherent ? tiny_rows<false, true>(P, r0, r1, keys_all, vals_all)
+                                  : tiny_rows<false, false>(P, r0, r1, keys_all, vals_all);
+            else
+                ok_all = coherent ? tiny_rows<true, true>(P, r0, r1, keys_all, vals_all)
+                                  : tiny_rows<true, false>(P, r0, r1, keys_all, vals_all);
+        }
+        for (int64_t rb = P.tiny ? r1 : r0; rb < r1; rb += RG) {
             const int64_t row = rb + g;
             const bool valid = row < r1;
             for (int s = lg; s < T; s += G) {

@@ -126,7 +126,11 @@ struct BatchProb {
     int64_t *crpt; int32_t *ccol; double *cval; int64_t ccap;
     int32_t ntiles;
     int32_t dep;        // product whose C is this B, -1 when B is an input
+    int32_t tiny;       // 1: every row has at most kBatchTiny products (one thread per row)
+    int32_t pad;
 };
+
+constexpr int kBatchTiny = 8;
 
 struct BatchItem {
     int32_t type;       // 0 symbolic tile, 1 scan, 2 numeric tile

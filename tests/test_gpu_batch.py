@@ -68,18 +68,23 @@ def test_independent_products_and_replay():
                     assert_values_close(val, want[2], want[3])
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
-def test_each_kernel_variant(variant):
+@pytest.mark.parametrize("variant,tiny", [(0, True), (0, False), (1, False), (2, False)])
+def test_each_kernel_variant(variant, tiny):
+    # tiny=False sends the A P products (at most 7 products per row) through
+    # the hash tables as well
     sides = [6, 9, 14]
     with ops.Handle() as h:
         As, Bs, dep, _ = galerkin_batch(h, sides)
-        with Batch(h, As, Bs, dep, variant=variant, tile_rows=64) as b:
+        with Batch(h, As, Bs, dep, variant=variant, tile_rows=64, tiny=tiny) as b:
             b.run()
             b.sync()
             assert b.info()["table"] in (64, 128, 256)
             for i, s in enumerate(sides):
                 A, P, PT = W.galerkin_problem(s)
                 APo = oracle.spgemm_csr(A, P)
+                rpt, col, val = _np(b.result(i))
+                assert np.array_equal(rpt, APo.rpt) and np.array_equal(col, APo.col)
+                assert np.array_equal(val, APo.val)
                 want = oracle.spgemm(PT, W.Csr(APo.rows, APo.cols, APo.rpt, APo.col, APo.val))
                 rpt, col, val = _np(b.result(len(sides) + i))
                 assert np.array_equal(col, want[1]) and np.array_equal(val, want[2])
