@@ -56,6 +56,13 @@ SLOT_NAMES = ([f"sym_bin{j}" for j in range(16)] + [f"num_bin{j}" for j in range
 NSLOTS = len(SLOT_NAMES)
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
+# of a workload's dominant kernel, from an ncu capture of this code (summary
+# and command in profiles/); None where no capture of the current kernel
+# exists.
+TRAFFIC = {("rmat20", "num_bitmap_kernel"): 222_989_678_080 + 205_420_339_456}
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -397,6 +404,12 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="also tune the bin configuration and time plain vs tuned")
     ap.add_argument("--save-config", default=None)
+    ap.add_argument("--rows", default=None,
+                    help="R0:R1 — measure only rows [R0, R1) of C (single GPU; for profiling "
+                         "a window of a workload too large to capture whole)")
+    ap.add_argument("--window-lists", type=int, default=None,
+                    help="set the numeric bitmap kernel's window_lists option on top of the "
+                         "configuration in use (0 = whole-row pass 2)")
     ap.add_argument("--legs", default="all", choices=["all", "none", "learned", "batched"],
                     help="extra comparisons after the main line: learned sizing vs plain "
                          "(trained weights) and 512 Galerkin products plain vs batched")
@@ -422,9 +435,22 @@ def main():
     desc, gen = WORKLOADS[args.workload]
     A = gen()
     r0, r1 = row_slab(A, rank, ws)
+    if args.rows:
+        if ws > 1:
+            raise SystemExit("--rows is for one GPU")
+        r0, r1 = (int(x) for x in args.rows.split(":"))
     dA = ops.CSR.from_workload(A, device=f"cuda:{local}")
     cfg = json.load(open(args.config)) if args.config else None
     h = ops.Handle(cfg)
+    if args.window_lists is not None:
+        # the configuration the handle uses for this B (the default one adapts
+        # its bins to B's columns at every symbolic call), with the option set
+        h.symbolic(dA, dA, r0, min(r1, r0 + 1))
+        C = h.numeric(dA, dA)
+        del C
+        cfg = h.get_config()
+        cfg["window_lists"] = args.window_lists
+        h.set_config(cfg)
     lib = _abi.lib()
     import ctypes
 
@@ -517,9 +543,21 @@ def main():
     avg_ms = kms[k] / launches
     peak, peak_kind = peaks()
     achieved = algo / (avg_ms / 1e3) / 1e9
+    # measured DRAM traffic of this launch where a capture of the same kernel,
+    # workload and configuration exists (the default one, whole matrix, 1 GPU)
+    traffic = traffic_src = None
+    cfg_now = h.get_config()
+    if k < 32 and k >= 16 and k - 16 == len(cfg_now["num_kernel"]) - 1 and ws == 1 \
+            and args.rows is None and not args.window_lists and args.config is None:
+        traffic = TRAFFIC.get((args.workload, "num_bitmap_kernel"))
+        if traffic is not None:
+            traffic_src = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch " \
+                          "(profiles/num_bitmap_kernel_rmat20.md)"
     roofline = {"bound": "hbm", "kernel": SLOT_NAMES[k], "achieved": round(achieved, 2),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
+                "traffic": traffic, "traffic_source": traffic_src,
+                "traffic_over_algorithmic": round(traffic / algo, 3) if traffic else None,
+                "peak_kind": f"{peak_kind} copy bandwidth",
                 "algorithmic_bytes_per_launch": int(algo), "avg_launch_ms": round(avg_ms, 4),
                 "serial_launch_ms": round(sms_[k] / max(sln[k], 1), 4),
                 "bytes_model": algo_desc}
