@@ -58,16 +58,60 @@ __device__ __forceinline__ int numeric_lanes(const Operands &op, int fixed, int6
     return pick_lanes_distinct(0, sum, p1 - p0, TPR);
 }
 
+// Ascending bitonic sort of the NR * 32 values one warp holds in registers,
+// element e = r * 32 + lane in x[r] (striped, so the sorted result stores
+// coalesced). Only the first P elements (a power of two >= 32) take part.
+// Strides below 32 exchange through shuffles, larger ones between a lane's
+// own registers (compile-time register indices only).
+template <int NR>
+__device__ __forceinline__ void warp_sort_striped(unsigned (&x)[NR], int P) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int jr = j >> 5;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+#pragma unroll
+                    for (int r2 = r + 1; r2 < NR; ++r2) {
+                        if (r2 == (r ^ jr) && r2 * 32 < P) {
+                            const bool up = ((r * 32 + lane) & k) == 0;
+                            const unsigned a = x[r], b = x[r2];
+                            if ((a > b) == up) {
+                                x[r] = b;
+                                x[r2] = a;
+                            }
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    if (r * 32 < P) {
+                        const unsigned o = __shfl_xor_sync(0xffffffffu, x[r], j);
+                        const bool up = ((r * 32 + lane) & k) == 0;
+                        const bool lower = (lane & j) == 0;
+                        const unsigned mn = x[r] < o ? x[r] : o, mx = x[r] < o ? o : x[r];
+                        x[r] = lower == up ? mn : mx;
+                    }
+                }
+            }
+        }
+    }
+}
+
 // Minimum resident blocks: enough for 2048 threads per SM (<= 32 registers
 // per thread, Sec. 5.6) unless the table is so large that one block fills
-// the SM's shared memory anyway.
+// the SM's shared memory anyway; warp-per-row kernels that sort in registers
+// get 1536 threads per SM (42 registers) so the sort does not spill.
 // ONE_PHASE (learned sizing): the row's size is not known; the table was
 // chosen from a prediction. A probe that finds no free slot, or more keys
 // than the table can sort in place, marks the row as mispredicted: it is
 // queued for the exact path and nothing is written. Otherwise the row's
 // size goes to C.rpt and its sorted entries to its temporary slot.
 template <int TPR, int BLOCK, int T, bool ONE_PHASE = false>
-__global__ void __launch_bounds__(BLOCK, (T * 12 * (BLOCK / TPR) > 110 * 1024) ? 1 : 2048 / BLOCK)
+__global__ void __launch_bounds__(BLOCK, (T * 12 * (BLOCK / TPR) > 110 * 1024) ? 1
+                                         : ((TPR == 32 && T <= 256) ? 1536 : 2048) / BLOCK)
 num_hash_kernel(Operands op, BinWork w) {
     constexpr int RPB = BLOCK / TPR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -158,6 +202,43 @@ num_hash_kernel(Operands op, BinWork w) {
         if (P > T) {  // cannot happen within the kernel's capacity; never index past the table
             set_error(w.err, DERR_TABLE_FULL);
             P = 1;
+        }
+    }
+    if constexpr (TPR == 32 && T <= 256) {
+        if (op.ncols <= (int64_t{1} << 24)) {   // uniform
+            // one warp per row: sort (column << 8 | slot) in registers, then
+            // store columns and the values of their slots in order
+            constexpr int NR = T / 32;
+            unsigned x[NR];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+                const int e = q * 32 + lg;
+                x[q] = e < n ? (static_cast<unsigned>(tk[e]) << 8) | static_cast<unsigned>(e) : 0xffffffffu;
+            }
+            int P2 = 32;
+            while (P2 < n) P2 <<= 1;
+            warp_sort_striped<NR>(x, P2);
+            if (valid) {
+                const int64_t m = n < n_expect ? n : n_expect;
+                int32_t *ocol = w.ccol + cbase;
+                double *oval = w.cval + cbase;
+                bool in_bounds = true;
+                if (ONE_PHASE) {
+                    ocol = w.tcol + w.tbase + r * w.tcap;
+                    oval = w.tval + w.tbase + r * w.tcap;
+                    in_bounds = m <= w.tcap && w.tbase + r * w.tcap + m <= w.tlimit;
+                    if (!in_bounds && lg == 0) set_error(w.err, DERR_BOUNDS);
+                }
+#pragma unroll
+                for (int q = 0; q < NR; ++q) {
+                    const int e = q * 32 + lg;
+                    if (in_bounds && e < m) {
+                        ocol[e] = static_cast<int32_t>(x[q] >> 8);
+                        oval[e] = tv[x[q] & 255u];
+                    }
+                }
+            }
+            return;   // uniform over the warp; no block barrier follows
         }
     }
     for (int s = n + lg; s < P; s += TPR) tk[s] = INT_MAX;

@@ -128,7 +128,7 @@ using SymFn = void (*)(Operands, BinWork);
     X(8, 256, 64)                    \
     X(16, 256, 256)                  \
     X(32, 256, 512)                  \
-    X(64, 64, 1024)                  \
+    X(32, 128, 1024)                 \
     X(128, 128, 2048)                \
     X(256, 256, 4096)                \
     X(512, 512, 8192)                \
