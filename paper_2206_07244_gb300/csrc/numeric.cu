@@ -60,42 +60,64 @@ __device__ __forceinline__ int numeric_lanes(const Operands &op, int fixed, int6
 
 // Ascending bitonic sort of the NR * 32 values one warp holds in registers,
 // element e = r * 32 + lane in x[r] (striped, so the sorted result stores
-// coalesced). Only the first P elements (a power of two >= 32) take part.
-// Strides below 32 exchange through shuffles, larger ones between a lane's
-// own registers (compile-time register indices only).
+// coalesced). Every loop has a compile-time trip count and unrolls fully, so
+// register indices are constants: strides below 32 exchange through
+// shuffles, larger ones between a lane's own registers.
 template <int NR>
-__device__ __forceinline__ void warp_sort_striped(unsigned (&x)[NR], int P) {
+__device__ __forceinline__ void warp_bitonic(unsigned (&x)[NR]) {
+    constexpr int P = NR * 32;
     const int lane = threadIdx.x & 31;
+#pragma unroll
     for (int k = 2; k <= P; k <<= 1) {
+#pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
             if (j >= 32) {
-                const int jr = j >> 5;
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
-#pragma unroll
-                    for (int r2 = r + 1; r2 < NR; ++r2) {
-                        if (r2 == (r ^ jr) && r2 * 32 < P) {
-                            const bool up = ((r * 32 + lane) & k) == 0;
-                            const unsigned a = x[r], b = x[r2];
-                            if ((a > b) == up) {
-                                x[r] = b;
-                                x[r2] = a;
-                            }
-                        }
+                    const int r2 = r ^ (j >> 5);
+                    if (r2 > r) {
+                        const bool up = ((r * 32 + lane) & k) == 0;
+                        const unsigned a = x[r], b = x[r2];
+                        const unsigned mn = a < b ? a : b, mx = a < b ? b : a;
+                        x[r] = up ? mn : mx;
+                        x[r2] = up ? mx : mn;
                     }
                 }
             } else {
+                const bool lower = (lane & j) == 0;
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
-                    if (r * 32 < P) {
-                        const unsigned o = __shfl_xor_sync(0xffffffffu, x[r], j);
-                        const bool up = ((r * 32 + lane) & k) == 0;
-                        const bool lower = (lane & j) == 0;
-                        const unsigned mn = x[r] < o ? x[r] : o, mx = x[r] < o ? o : x[r];
-                        x[r] = lower == up ? mn : mx;
-                    }
+                    const unsigned o = __shfl_xor_sync(0xffffffffu, x[r], j);
+                    const bool up = ((r * 32 + lane) & k) == 0;
+                    const unsigned mn = x[r] < o ? x[r] : o, mx = x[r] < o ? o : x[r];
+                    x[r] = lower == up ? mn : mx;
                 }
             }
+        }
+    }
+}
+
+// One warp: sort the n condensed entries (tk[e], tv[e]), e < n <= NR * 32,
+// by column and store the first m to ocol/oval. Keys are (column << 8 | e):
+// columns below 2^24, n <= 256.
+template <int NR>
+__device__ __forceinline__ void warp_sort_store(const int *tk, const double *tv, int n, int64_t m,
+                                                int32_t *ocol, double *oval, bool store) {
+    const int lane = threadIdx.x & 31;
+    unsigned x[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+        const int e = q * 32 + lane;
+        x[q] = e < n ? (static_cast<unsigned>(tk[e]) << 8) | static_cast<unsigned>(e) : 0xffffffffu;
+    }
+    warp_bitonic<NR>(x);
+    if (!store) return;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+        const int e = q * 32 + lane;
+        if (e < m) {
+            ocol[e] = static_cast<int32_t>(x[q] >> 8);
+            oval[e] = tv[x[q] & 255u];
         }
     }
 }
@@ -208,36 +230,21 @@ num_hash_kernel(Operands op, BinWork w) {
         if (op.ncols <= (int64_t{1} << 24)) {   // uniform
             // one warp per row: sort (column << 8 | slot) in registers, then
             // store columns and the values of their slots in order
-            constexpr int NR = T / 32;
-            unsigned x[NR];
-#pragma unroll
-            for (int q = 0; q < NR; ++q) {
-                const int e = q * 32 + lg;
-                x[q] = e < n ? (static_cast<unsigned>(tk[e]) << 8) | static_cast<unsigned>(e) : 0xffffffffu;
+            const int64_t m = n < n_expect ? n : n_expect;
+            int32_t *ocol = w.ccol + cbase;
+            double *oval = w.cval + cbase;
+            bool in_bounds = true;
+            if (ONE_PHASE) {
+                ocol = w.tcol + w.tbase + r * w.tcap;
+                oval = w.tval + w.tbase + r * w.tcap;
+                in_bounds = m <= w.tcap && w.tbase + r * w.tcap + m <= w.tlimit;
+                if (valid && !in_bounds && lg == 0) set_error(w.err, DERR_BOUNDS);
             }
-            int P2 = 32;
-            while (P2 < n) P2 <<= 1;
-            warp_sort_striped<NR>(x, P2);
-            if (valid) {
-                const int64_t m = n < n_expect ? n : n_expect;
-                int32_t *ocol = w.ccol + cbase;
-                double *oval = w.cval + cbase;
-                bool in_bounds = true;
-                if (ONE_PHASE) {
-                    ocol = w.tcol + w.tbase + r * w.tcap;
-                    oval = w.tval + w.tbase + r * w.tcap;
-                    in_bounds = m <= w.tcap && w.tbase + r * w.tcap + m <= w.tlimit;
-                    if (!in_bounds && lg == 0) set_error(w.err, DERR_BOUNDS);
-                }
-#pragma unroll
-                for (int q = 0; q < NR; ++q) {
-                    const int e = q * 32 + lg;
-                    if (in_bounds && e < m) {
-                        ocol[e] = static_cast<int32_t>(x[q] >> 8);
-                        oval[e] = tv[x[q] & 255u];
-                    }
-                }
-            }
+            const bool store = valid && in_bounds;
+            if (n <= 32) warp_sort_store<1>(tk, tv, n, m, ocol, oval, store);
+            else if (n <= 64) warp_sort_store<2>(tk, tv, n, m, ocol, oval, store);
+            else if (n <= 128 || T <= 128) warp_sort_store<(T < 128 ? T / 32 : 4)>(tk, tv, n, m, ocol, oval, store);
+            else warp_sort_store<T / 32>(tk, tv, n, m, ocol, oval, store);
             return;   // uniform over the warp; no block barrier follows
         }
     }
