@@ -60,7 +60,7 @@ NSLOTS = len(SLOT_NAMES)
 # of a workload's dominant kernel, from an ncu capture of this code (summary
 # and command in profiles/); None where no capture of the current kernel
 # exists.
-TRAFFIC = {("rmat20", "num_bitmap_kernel"): 222_989_678_080 + 205_420_339_456}
+TRAFFIC = {}
 
 
 def peaks():

@@ -288,6 +288,52 @@ num_hash_kernel(Operands op, BinWork w) {
     }
 }
 
+// Rank of every bitmap word's first column: pre[i] = set bits in words
+// [0, i). Warp w owns words [w * per, (w + 1) * per) (per a multiple of 32)
+// and its lanes read consecutive words, so no two lanes of a warp hit one
+// bank. Returns the total. Synchronises the block; pre is complete on return.
+template <int BLOCK>
+__device__ __forceinline__ unsigned bitmap_ranks(const unsigned long long *bm, unsigned *pre, int nw,
+                                                 unsigned *sw) {
+    constexpr int kWarps = BLOCK / 32;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int per = (((nw + kWarps - 1) / kWarps) + 31) & ~31;
+    const int w0 = wp * per;
+    const int w1 = w0 + per < nw ? w0 + per : nw;
+    unsigned cnt = 0;
+    for (int i = w0 + lane; i < w1; i += 32) cnt += static_cast<unsigned>(__popcll(bm[i]));
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    __syncthreads();   // earlier readers of sw are done
+    if (lane == 0) sw[wp] = cnt;
+    __syncthreads();
+    if (wp == 0) {
+        const unsigned t = lane < kWarps ? sw[lane] : 0u;
+        unsigned inc = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane < kWarps) sw[lane] = inc - t;
+        if (lane == 31) sw[32] = inc;
+    }
+    __syncthreads();
+    unsigned base = sw[wp];
+    const unsigned total = sw[32];
+    for (int i0 = w0; i0 < w1; i0 += 32) {
+        const int i = i0 + lane;
+        const unsigned c = i < w1 ? static_cast<unsigned>(__popcll(bm[i])) : 0u;
+        unsigned inc = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (i < w1) pre[i] = base + inc - c;
+        base += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    __syncthreads();
+    return total;
+}
+
 // Pass 2 by column windows (B rows sorted, run boundaries from bsplit): the
 // row's products whose columns fall in sub-ranges [g, g2) of the column
 // space are, per A entry, one run of its B row; the runs of a window are
@@ -395,24 +441,10 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
             if (rel < span32) atomicOr(bm32 + (rel >> 5), 1u << (rel & 31));
         });
         // per-word prefix counts = rank of a word's first column in the
-        // window; thread t owns a contiguous run of words, so one block scan
-        // of the per-thread counts suffices
-        unsigned run = 0;
-        {
-            const int per = (nw + kBmBlock - 1) / kBmBlock;
-            const int i0 = static_cast<int>(threadIdx.x) * per;
-            const int i1 = i0 + per < nw ? i0 + per : nw;
-            unsigned c = 0;
-            for (int i = i0; i < i1; ++i) c += static_cast<unsigned>(__popcll(bm[i]));
-            unsigned tot;
-            unsigned ex = block_excl_scan<kBmBlock>(c, tot, sw);
-            for (int i = i0; i < i1; ++i) {
-                pre[i] = ex;
-                ex += static_cast<unsigned>(__popcll(bm[i]));
-            }
-            run = tot;
-        }
-        __syncthreads();
+        // window. Warps own contiguous ranges of words and their lanes read
+        // consecutive words (no bank conflicts): a warp scan per 32 words,
+        // one block scan of the warp totals.
+        const unsigned run = bitmap_ranks<kBmBlock>(bm, pre, nw, sw);
         const int64_t cnt = run;
         if (done + cnt > n_expect) ok = false;   // uniform: cnt and done are block-wide
         if (ok) {
