@@ -183,11 +183,15 @@ typedef int (*spgemm_host_sink_fn)(void *ctx, int64_t row_begin, int64_t rows,
 
 /* C = A * B for operands in HOST memory (pinned memory gives full copy
  * speed): copies A and B to the device (once if A and B are the same
- * arrays), runs spgemm_multiply, then streams C back in chunks of at most
- * chunk_bytes of (col, val) through two pinned staging buffers, calling
- * sink for each chunk in row order while the next chunk is in flight. C
- * never has to fit in host memory. *nnzC (may be NULL) receives the total.
- * Device copies and C are released before returning. */
+ * arrays), then computes C in slabs of rows with about equal n_prod (about
+ * 1.5e9 products each, and at least one slab per 8 chunks of C at the
+ * n_prod bound, at most 64) and streams each slab back in chunks of at most
+ * chunk_bytes of (col, val) through two pinned staging buffers, on streams
+ * of their own, while the next slab is computed. sink is called for each
+ * chunk in row order while the next chunk is in flight. Neither C nor more
+ * than two slabs of it have to fit in host or device memory. *nnzC (may be
+ * NULL) receives the total. Device copies and C are released before
+ * returning. */
 int spgemm_multiply_host(spgemm_handle *h, const spgemm_csr_in *A,
                          const spgemm_csr_in *B, int64_t chunk_bytes,
                          spgemm_host_sink_fn sink, void *ctx, int64_t *nnzC);

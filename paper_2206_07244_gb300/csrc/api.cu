@@ -68,6 +68,7 @@ struct spgemm_handle {
     int smem_dyn_max = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t side[kSide] = {};
+    cudaStream_t copyst[2] = {};   // device -> host copies of spgemm_multiply_host
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_side[kSide] = {};
     spgemm_alloc_fn alloc = nullptr;
@@ -1003,10 +1004,12 @@ int spgemm_multiply_host(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_
     if (A->cols != B->rows) return SPGEMM_ERR_SHAPE;
     if ((A->nnz > 0 && !A->val) || (B->nnz > 0 && !B->val)) return SPGEMM_ERR_INVALID;
     if (chunk_bytes < (1 << 20)) chunk_bytes = 1 << 20;
+    for (auto &cs : h->copyst)
+        if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return SPGEMM_ERR_CUDA;
     const bool same = A->rpt == B->rpt && A->col == B->col && A->val == B->val &&
                       A->rows == B->rows && A->rpt_is_i64 == B->rpt_is_i64;
     // host -> device copies of the operands
-    void *dev[6] = {};
+    void *dev[7] = {};
     auto release = [&]() {
         for (void *p : dev) dev_free(h, p);
     };
@@ -1033,24 +1036,55 @@ int spgemm_multiply_host(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_
     if ((rc = upload(A, dev, &dA))) { release(); return rc; }
     if (same) dB = dA;
     else if ((rc = upload(B, dev + 3, &dB))) { release(); return rc; }
-    int64_t nnz = 0;
-    if ((rc = spgemm_symbolic(h, &dA, &dB, 0, A->rows, &nnz))) { release(); return rc; }
-    spgemm_csr_out C{};
-    if ((rc = spgemm_numeric(h, &dA, &dB, &C))) { release(); return rc; }
-    auto release_all = [&]() {
-        release();
-        dev_free(h, C.rpt);
-        dev_free(h, C.col);
-        dev_free(h, C.val);
-    };
-    // pinned staging: the whole row pointer plus two chunk buffers
-    const size_t nr = (size_t)C.rows + 1;
+    const int64_t M = A->rows;
+
+    // Slabs of rows with about equal n_prod: slab s + 1 is computed while
+    // slab s is copied to the host, so the copies (bound by the host link)
+    // hide the arithmetic.
+    std::vector<int64_t> cut{0, M};
+    if (M > 1) {
+        int64_t *d_np = static_cast<int64_t *>(dev_alloc(h, sizeof(int64_t) * (size_t)M));
+        dev[6] = d_np;
+        if (!d_np) { release(); return SPGEMM_ERR_OOM; }
+        const Operands op = make_operands(&dA, &dB, 0, M);
+        std::vector<int64_t> np((size_t)M);
+        if (cudaMemsetAsync(d_np, 0, sizeof(int64_t) * (size_t)M, h->stream) != cudaSuccess ||
+            note(launch_nprod(op, d_np, h->sm_count * 8, h->stream)) != cudaSuccess ||
+            cudaMemcpyAsync(np.data(), d_np, sizeof(int64_t) * (size_t)M, cudaMemcpyDeviceToHost,
+                            h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            release();
+            return SPGEMM_ERR_CUDA;
+        }
+        long double total = 0;
+        for (int64_t v : np) total += (long double)v;
+        // about 1.5e9 products per slab, and at least one slab per 8 chunks
+        // of C at the n_prod upper bound (12 bytes per entry)
+        const long double by_work = total / 1.5e9L;
+        const long double by_copy = 12.0L * total / (8.0L * (long double)chunk_bytes);
+        const int S = static_cast<int>(std::min<long double>(64, std::max<long double>(1, std::max(by_work, by_copy))));
+        cut.assign(1, 0);
+        long double acc = 0;
+        for (int64_t r = 0; r < M; ++r) {
+            acc += (long double)np[(size_t)r];
+            if ((int)cut.size() < S && acc >= total * (long double)cut.size() / S) cut.push_back(r + 1);
+        }
+        if (cut.back() != M) cut.push_back(M);
+        dev_free(h, d_np);
+        dev[6] = nullptr;
+    }
+    const int S = static_cast<int>(cut.size()) - 1;
+
+    // pinned staging: row pointers of one slab plus two chunk buffers
+    int64_t max_rows = 0;
+    for (int k = 0; k < S; ++k) max_rows = std::max(max_rows, cut[k + 1] - cut[k]);
+    const size_t nr = (size_t)max_rows + 1;
     if (h->stage_rpt_n < nr) {
         if (h->stage_rpt) cudaFreeHost(h->stage_rpt);
         h->stage_rpt = nullptr;
         h->stage_rpt_n = 0;
         if (cudaMallocHost(&h->stage_rpt, sizeof(int64_t) * nr) != cudaSuccess) {
-            release_all();
+            release();
             return SPGEMM_ERR_OOM;
         }
         h->stage_rpt_n = nr;
@@ -1060,112 +1094,139 @@ int spgemm_multiply_host(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_
         h->stage = nullptr;
         h->stage_bytes = 0;
         if (cudaMallocHost(&h->stage, 2 * (size_t)chunk_bytes) != cudaSuccess) {
-            release_all();
+            release();
             return SPGEMM_ERR_OOM;
         }
         h->stage_bytes = 2 * (size_t)chunk_bytes;
     }
-    if (cudaMemcpyAsync(h->stage_rpt, C.rpt, sizeof(int64_t) * nr, cudaMemcpyDeviceToHost, h->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(h->stream) != cudaSuccess) {
-        release_all();
+    cudaEvent_t ev_c[2] = {}, part_done[2][2] = {};
+    auto destroy_events = [&]() {
+        for (auto &e : ev_c)
+            if (e) cudaEventDestroy(e);
+        for (auto &row : part_done)
+            for (auto &e : row)
+                if (e) cudaEventDestroy(e);
+    };
+    bool ev_ok = true;
+    for (auto &e : ev_c) ev_ok &= cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    for (auto &row : part_done)
+        for (auto &e : row) ev_ok &= cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ev_ok) {
+        destroy_events();
+        release();
         return SPGEMM_ERR_CUDA;
     }
-    const int64_t *rpt = h->stage_rpt;
-    // rows per chunk: as many as fit in chunk_bytes of (col, val), at least one
-    struct Chunk { int64_t r0, r1; };
-    auto next_chunk = [&](int64_t r0) {
-        int64_t r1 = r0 + 1;
-        int64_t lo = r0 + 1, hi = C.rows;
-        while (lo <= hi) {  // largest r1 with 12 * (rpt[r1] - rpt[r0]) <= chunk_bytes
+
+    spgemm_csr_out C[2] = {};
+    int64_t nnz_s[2] = {0, 0};
+    auto free_c = [&](int b) {
+        dev_free(h, C[b].rpt);
+        dev_free(h, C[b].col);
+        dev_free(h, C[b].val);
+        C[b] = spgemm_csr_out{};
+    };
+    auto compute = [&](int k) -> int {
+        const int b = k & 1;
+        int r = spgemm_symbolic(h, &dA, &dB, cut[k], cut[k + 1], &nnz_s[b]);
+        if (r) return r;
+        if ((r = spgemm_numeric(h, &dA, &dB, &C[b]))) return r;
+        CK(cudaEventRecord(ev_c[b], h->stream));
+        return SPGEMM_OK;
+    };
+    // chunk copies: (col, val) of rows [r0, r1) of the slab in buffer `buf`,
+    // split over the two copy streams
+    int64_t *rpt = h->stage_rpt;
+    // a chunk of n entries holds n columns, padding to 256 bytes, n values
+    auto fits = [&](int64_t n) { return ((4 * n + 255) & ~int64_t{255}) + 8 * n <= chunk_bytes; };
+    auto next_rows = [&](int64_t r0, int64_t rows) {
+        int64_t r1 = r0 + 1, lo = r0 + 1, hi = rows;
+        while (lo <= hi) {   // largest r1 whose entries fit one chunk
             const int64_t mid = lo + (hi - lo) / 2;
-            if (12 * (rpt[mid] - rpt[r0]) <= chunk_bytes) { r1 = mid; lo = mid + 1; }
+            if (fits(rpt[mid] - rpt[r0])) { r1 = mid; lo = mid + 1; }
             else hi = mid - 1;
         }
-        return Chunk{r0, r1};
+        return r1;
     };
-    cudaEvent_t done[2] = {};
-    for (auto &e : done)
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-            release_all();
-            return SPGEMM_ERR_CUDA;
-        }
-    // Each chunk's copy is split into kCopyParts pieces on the side streams,
-    // so several copy engines move it at once.
-    constexpr int kCopyParts = 4;
-    cudaEvent_t part_done[2][kCopyParts] = {};
-    for (auto &row : part_done)
-        for (auto &e : row)
-            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-                release_all();
-                return SPGEMM_ERR_CUDA;
-            }
-    if (cudaEventRecord(h->ev_fork, h->stream) != cudaSuccess) {
-        release_all();
-        return SPGEMM_ERR_CUDA;
-    }
-    for (int k = 0; k < kCopyParts; ++k) cudaStreamWaitEvent(h->side[k], h->ev_fork, 0);
-    auto enqueue = [&](const Chunk &c, int b) -> bool {
-        const int64_t n = rpt[c.r1] - rpt[c.r0];
-        if (12 * n > chunk_bytes) return false;  // one row larger than a chunk
-        unsigned char *buf = h->stage + (size_t)b * (size_t)chunk_bytes;
-        int32_t *hcol = reinterpret_cast<int32_t *>(buf);
-        double *hval = reinterpret_cast<double *>(buf + ((sizeof(int32_t) * (size_t)n + 255) & ~size_t(255)));
-        // the host may still be reading buffer b from two chunks ago: the
-        // sink for it returned before this enqueue, so it is free now
-        for (int k = 0; k < kCopyParts; ++k) {
-            const int64_t lo = n * k / kCopyParts, hi = n * (k + 1) / kCopyParts;
-            cudaStream_t s = h->side[k];
-            if (hi > lo) {
-                if (cudaMemcpyAsync(hcol + lo, C.col + rpt[c.r0] + lo, sizeof(int32_t) * (size_t)(hi - lo),
-                                    cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                    cudaMemcpyAsync(hval + lo, C.val + rpt[c.r0] + lo, sizeof(double) * (size_t)(hi - lo),
-                                    cudaMemcpyDeviceToHost, s) != cudaSuccess)
-                    return false;
-            }
-            if (cudaEventRecord(part_done[b][k], s) != cudaSuccess) return false;
+    auto enqueue = [&](const spgemm_csr_out &c, int64_t r0, int64_t r1, int buf) -> bool {
+        const int64_t n = rpt[r1] - rpt[r0];
+        if (!fits(n)) return false;   // one row larger than a chunk
+        unsigned char *base = h->stage + (size_t)buf * (size_t)chunk_bytes;
+        int32_t *hcol = reinterpret_cast<int32_t *>(base);
+        double *hval = reinterpret_cast<double *>(base + ((sizeof(int32_t) * (size_t)n + 255) & ~size_t(255)));
+        const int64_t off = rpt[r0] - rpt[0];
+        for (int k = 0; k < 2; ++k) {
+            const int64_t lo = n * k / 2, hi = n * (k + 1) / 2;
+            cudaStream_t cs = h->copyst[k];
+            if (hi > lo &&
+                (cudaMemcpyAsync(hcol + lo, c.col + off + lo, sizeof(int32_t) * (size_t)(hi - lo),
+                                 cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+                 cudaMemcpyAsync(hval + lo, c.val + off + lo, sizeof(double) * (size_t)(hi - lo),
+                                 cudaMemcpyDeviceToHost, cs) != cudaSuccess))
+                return false;
+            if (cudaEventRecord(part_done[buf][k], cs) != cudaSuccess) return false;
         }
         return true;
     };
-    auto wait_chunk = [&](int b) -> bool {
-        for (int k = 0; k < kCopyParts; ++k)
-            if (cudaEventSynchronize(part_done[b][k]) != cudaSuccess) return false;
+    auto wait_buf = [&](int buf) -> bool {
+        for (int k = 0; k < 2; ++k)
+            if (cudaEventSynchronize(part_done[buf][k]) != cudaSuccess) return false;
         return true;
     };
-    rc = SPGEMM_OK;
-    if (C.rows > 0) {
-        Chunk cur = next_chunk(0);
-        if (!enqueue(cur, 0)) rc = SPGEMM_ERR_INVALID;
-        int b = 0;
-        while (rc == SPGEMM_OK) {
-            Chunk nxt{cur.r1, cur.r1};
-            const bool more = cur.r1 < C.rows;
+
+    rc = S > 0 ? compute(0) : SPGEMM_OK;
+    int64_t nnz_total = 0, nnz_before = 0;
+    for (int k = 0; k < S && rc == SPGEMM_OK; ++k) {
+        const int b = k & 1;
+        const int64_t rows = cut[k + 1] - cut[k];
+        // slab k's row pointers (the copy streams wait for its kernels)
+        bool ok = true;
+        for (auto &cs : h->copyst) ok &= cudaStreamWaitEvent(cs, ev_c[b], 0) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(rpt, C[b].rpt, sizeof(int64_t) * (size_t)(rows + 1), cudaMemcpyDeviceToHost,
+                                   h->copyst[0]) == cudaSuccess &&
+             cudaStreamSynchronize(h->copyst[0]) == cudaSuccess;
+        if (!ok) { rc = SPGEMM_ERR_CUDA; break; }
+        if (rows > 0 && rpt[rows] - rpt[0] != nnz_s[b]) { rc = SPGEMM_ERR_INTERNAL; break; }
+        int64_t r0 = 0, r1 = rows > 0 ? next_rows(0, rows) : 0;
+        int buf = 0;
+        if (rows > 0 && !enqueue(C[b], r0, r1, buf)) { rc = SPGEMM_ERR_INVALID; break; }
+        // the next slab's kernels run while this slab's copies are in flight
+        if (k + 1 < S && (rc = compute(k + 1))) break;
+        while (rows > 0) {
+            const bool more = r1 < rows;
+            int64_t n0 = r1, n1 = r1;
             if (more) {
-                nxt = next_chunk(cur.r1);
-                if (!enqueue(nxt, b ^ 1)) { rc = SPGEMM_ERR_INVALID; break; }
+                n1 = next_rows(n0, rows);
+                if (!enqueue(C[b], n0, n1, buf ^ 1)) { rc = SPGEMM_ERR_INVALID; break; }
             }
-            if (!wait_chunk(b)) { rc = SPGEMM_ERR_CUDA; break; }
-            const int64_t n = rpt[cur.r1] - rpt[cur.r0];
-            unsigned char *buf = h->stage + (size_t)b * (size_t)chunk_bytes;
-            const int32_t *hc = reinterpret_cast<const int32_t *>(buf);
+            if (!wait_buf(buf)) { rc = SPGEMM_ERR_CUDA; break; }
+            const int64_t n = rpt[r1] - rpt[r0];
+            unsigned char *base = h->stage + (size_t)buf * (size_t)chunk_bytes;
+            const int32_t *hc = reinterpret_cast<const int32_t *>(base);
             const double *hv = reinterpret_cast<const double *>(
-                buf + ((sizeof(int32_t) * (size_t)n + 255) & ~size_t(255)));
-            if (sink(ctx, cur.r0, cur.r1 - cur.r0, rpt + cur.r0, hc, hv, n) != 0) {
-                rc = SPGEMM_ERR_ABORTED;
-                break;
-            }
+                base + ((sizeof(int32_t) * (size_t)n + 255) & ~size_t(255)));
+            // row pointers handed over are absolute in the whole C
+            const int64_t shift = nnz_before - rpt[0];
+            for (int64_t i = r0; i <= r1; ++i) rpt[i] += shift;
+            const int sr = sink(ctx, cut[k] + r0, r1 - r0, rpt + r0, hc, hv, n);
+            for (int64_t i = r0; i <= r1; ++i) rpt[i] -= shift;
+            if (sr != 0) { rc = SPGEMM_ERR_ABORTED; break; }
             if (!more) break;
-            cur = nxt;
-            b ^= 1;
+            r0 = n0;
+            r1 = n1;
+            buf ^= 1;
         }
+        if (rc != SPGEMM_OK) break;
+        nnz_before += nnz_s[b];
+        nnz_total += nnz_s[b];
+        free_c(b);
     }
-    for (int k = 0; k < kCopyParts; ++k) cudaStreamSynchronize(h->side[k]);
+    for (auto &cs : h->copyst) cudaStreamSynchronize(cs);
     cudaStreamSynchronize(h->stream);
-    for (auto &e : done) cudaEventDestroy(e);
-    for (auto &row : part_done)
-        for (auto &e : row) cudaEventDestroy(e);
-    release_all();
-    if (rc == SPGEMM_OK && nnzC) *nnzC = nnz;
+    free_c(0);
+    free_c(1);
+    destroy_events();
+    release();
+    if (rc == SPGEMM_OK && nnzC) *nnzC = nnz_total;
     return rc;
 }
 
@@ -1249,6 +1310,8 @@ int spgemm_destroy(spgemm_handle *h) {
         if (h->side[i]) cudaStreamDestroy(h->side[i]);
         if (h->ev_side[i]) cudaEventDestroy(h->ev_side[i]);
     }
+    for (auto &cs : h->copyst)
+        if (cs) cudaStreamDestroy(cs);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     for (int k = 0; k < kSlots; ++k) {
         if (h->t0[k]) cudaEventDestroy(h->t0[k]);
