@@ -60,7 +60,7 @@ NSLOTS = len(SLOT_NAMES)
 # of a workload's dominant kernel, from an ncu capture of this code (summary
 # and command in profiles/); None where no capture of the current kernel
 # exists.
-TRAFFIC = {}
+TRAFFIC = {("rmat20", "num_bitmap_kernel"): 237_253_962_240 + 215_449_080_320}
 
 
 def peaks():
