@@ -298,7 +298,7 @@ typedef struct spgemm_batch spgemm_batch;
 typedef struct {
     int32_t variant;     /* -1: smallest table that holds the largest row;
                             0, 1, 2: 8 lanes / 64 slots, 16 / 128, 32 / 256 */
-    int32_t tile_rows;   /* rows per work item (0: 32 per row group)       */
+    int32_t tile_rows;   /* rows per work item, at most 1024 (0: 32 per row group) */
     int64_t spin_limit;  /* polls of a bounded wait, 200 ns apart (0: 2^22) */
     int32_t no_tiny;     /* 1: products whose rows have at most 8 products
                             also use the hash tables (0: one thread per row) */

@@ -1475,11 +1475,14 @@ int spgemm_batch_create(spgemm_batch **out, spgemm_handle *h, int n, const spgem
     const int rg = 256 / batch_variant_lanes(b->variant);
     b->tile_rows = (opt && opt->tile_rows > 0) ? opt->tile_rows : rg * 32;
     if (b->tile_rows % rg) b->tile_rows += rg - b->tile_rows % rg;
+    if (b->tile_rows > kBatchMaxTile) return fail(SPGEMM_ERR_INVALID);
     b->spin_limit = (opt && opt->spin_limit > 0) ? opt->spin_limit : (1LL << 22);
     // arena: per product C.rpt (M+1 int64), C.col and C.val with room for the bound
-    std::vector<size_t> off_rpt(n), off_col(n), off_val(n);
+    std::vector<size_t> off_rpt(n), off_col(n), off_val(n), off_tsum(n);
     size_t total = 0;
     for (int i = 0; i < n; ++i) {
+        const int64_t nt = (b->M[i] + b->tile_rows - 1) / b->tile_rows;
+        off_tsum[i] = total; total += align256(sizeof(long long) * (size_t)(nt + 1));
         off_rpt[i] = total; total += align256(sizeof(int64_t) * (size_t)(b->M[i] + 1));
         off_col[i] = total; total += align256(sizeof(int32_t) * (size_t)std::max<int64_t>(cap[i], 1));
         off_val[i] = total; total += align256(sizeof(double) * (size_t)std::max<int64_t>(cap[i], 1));
@@ -1501,6 +1504,7 @@ int spgemm_batch_create(spgemm_batch **out, spgemm_handle *h, int n, const spgem
         P.ccol = reinterpret_cast<int32_t *>(b->arena + off_col[i]);
         P.cval = reinterpret_cast<double *>(b->arena + off_val[i]);
         P.ccap = cap[i];
+        P.tsum = reinterpret_cast<long long *>(b->arena + off_tsum[i]);
         P.ntiles = static_cast<int32_t>((P.M + b->tile_rows - 1) / b->tile_rows);
         P.dep = dep;
         P.tiny = pmax[i] <= kBatchTiny && !(opt && opt->no_tiny) ? 1 : 0;

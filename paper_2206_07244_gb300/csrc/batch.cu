@@ -1,5 +1,10 @@
 // Batched SpGEMM: many products with small rows in one persistent launch.
 //
+// Row offsets without a serial scan: a symbolic tile also stores the sum
+// of its rows' sizes (tsum[tile]); the scan item of a product scans only
+// those tile sums; a numeric tile turns its own rows' sizes into offsets
+// (tile prefix + block scan) and writes them to C.rpt before it multiplies.
+//
 // A batch is a list of products C_i = A_i * B_i in which B_i may be the C of
 // an earlier product (a chain such as the Galerkin product P^T (A P) of
 // algebraic multigrid). Per product the two-phase method of Sec. 2.2 runs as
@@ -108,7 +113,8 @@ __device__ __forceinline__ bool batch_row(const BatchProb &P, int64_t row, int *
 // order; the row is then stored as it stands, without condense or sort.
 template <bool NUMERIC, bool COHERENT>
 __device__ __forceinline__ bool tiny_rows(const BatchProb &P, int64_t r0, int64_t r1, int *keys,
-                                          double *vals) {
+                                          double *vals, const long long *offs, const int *cnts,
+                                          long long &tile_sum) {
     bool ok = true;
     const int t = threadIdx.x;
     for (int64_t row = r0 + t; row < r1; row += kBatchBlock) {
@@ -142,9 +148,10 @@ __device__ __forceinline__ bool tiny_rows(const BatchProb &P, int64_t r0, int64_
         }
         if (!NUMERIC) {
             P.crpt[row] = n;
+            tile_sum += n;
         } else {
-            const int64_t base = __ldcg(reinterpret_cast<const long long *>(P.crpt) + row);
-            const int64_t want = __ldcg(reinterpret_cast<const long long *>(P.crpt) + row + 1) - base;
+            const int64_t base = offs[row - r0];
+            const int64_t want = cnts[row - r0];
             if (want != n || base + n > P.ccap) {
                 ok = false;
             } else {
@@ -166,6 +173,8 @@ batch_kernel(const BatchProb *probs, const BatchItem *items, int nitems, BatchSt
     static_assert(RG * T >= kBatchTiny * kBatchBlock, "tiny rows reuse the tables");
     __shared__ int keys_all[RG * T];
     __shared__ double vals_all[RG * T];
+    __shared__ long long offs[kBatchMaxTile];   // numeric tile: offset of each row in C
+    __shared__ int cnts[kBatchMaxTile];         // numeric tile: size of each row
     __shared__ int red32[33];
     __shared__ long long red64[33];   // block scan: one slot per warp + the total
     __shared__ int s_item;
@@ -197,15 +206,15 @@ batch_kernel(const BatchProb *probs, const BatchItem *items, int nitems, BatchSt
         __syncthreads();
         if (!s_ok) return;
         if (I.type == 1) {
-            // exclusive scan of C.rpt[0..M) in place, C.rpt[M] = total
+            // exclusive scan of the tile sums in place; C.rpt[M] = total
             if (threadIdx.x == 0) s_run = 0;
             __syncthreads();
-            for (int64_t b = 0; b < P.M; b += kBatchBlock) {
+            for (int64_t b = 0; b < P.ntiles; b += kBatchBlock) {
                 const int64_t i = b + threadIdx.x;
-                const long long v = i < P.M ? __ldcg(reinterpret_cast<const long long *>(P.crpt) + i) : 0;
+                const long long v = i < P.ntiles ? __ldcg(P.tsum + i) : 0;
                 long long tot;
                 const long long ex = block_excl_scan_ll<kBatchBlock>(v, tot, red64);
-                if (i < P.M) P.crpt[i] = s_run + ex;
+                if (i < P.ntiles) P.tsum[i] = s_run + ex;
                 __syncthreads();
                 if (threadIdx.x == 0) s_run += tot;
                 __syncthreads();
@@ -222,13 +231,41 @@ batch_kernel(const BatchProb *probs, const BatchItem *items, int nitems, BatchSt
         const int64_t r1 = r0 + tile_rows < P.M ? r0 + tile_rows : P.M;
         const bool coherent = P.dep >= 0;
         bool ok_all = true;
+        long long tile_sum = 0;   // symbolic: this thread's share of the tile's n_nz
+        if (I.type == 2) {
+            // row offsets of the tile: its prefix from the scan plus a block
+            // scan of its rows' sizes (each thread four consecutive rows)
+            constexpr int kPer = kBatchMaxTile / kBatchBlock;
+            const int64_t nrow = r1 - r0;
+            long long c[kPer];
+            long long part = 0;
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int64_t i = static_cast<int64_t>(threadIdx.x) * kPer + q;
+                c[q] = i < nrow ? __ldcg(reinterpret_cast<const long long *>(P.crpt) + r0 + i) : 0;
+                part += c[q];
+            }
+            long long tot;
+            long long ex = block_excl_scan_ll<kBatchBlock>(part, tot, red64) + __ldcg(P.tsum + I.tile);
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int64_t i = static_cast<int64_t>(threadIdx.x) * kPer + q;
+                if (i < nrow) {
+                    offs[i] = ex;
+                    cnts[i] = static_cast<int>(c[q]);
+                    P.crpt[r0 + i] = ex;
+                }
+                ex += c[q];
+            }
+            __syncthreads();
+        }
         if (P.tiny) {
             if (I.type == 0)
-                ok_all = coherent ? tiny_rows<false, true>(P, r0, r1, keys_all, vals_all)
-                                  : tiny_rows<false, false>(P, r0, r1, keys_all, vals_all);
+                ok_all = coherent ? tiny_rows<false, true>(P, r0, r1, keys_all, vals_all, offs, cnts, tile_sum)
+                                  : tiny_rows<false, false>(P, r0, r1, keys_all, vals_all, offs, cnts, tile_sum);
             else
-                ok_all = coherent ? tiny_rows<true, true>(P, r0, r1, keys_all, vals_all)
-                                  : tiny_rows<true, false>(P, r0, r1, keys_all, vals_all);
+                ok_all = coherent ? tiny_rows<true, true>(P, r0, r1, keys_all, vals_all, offs, cnts, tile_sum)
+                                  : tiny_rows<true, false>(P, r0, r1, keys_all, vals_all, offs, cnts, tile_sum);
         }
         for (int64_t rb = P.tiny ? r1 : r0; rb < r1; rb += RG) {
             const int64_t row = rb + g;
@@ -244,7 +281,10 @@ batch_kernel(const BatchProb *probs, const BatchItem *items, int nitems, BatchSt
                 if (valid) ok = coherent ? batch_row<G, T, false, true>(P, row, tk, tv, lg, cnt)
                                          : batch_row<G, T, false, false>(P, row, tk, tv, lg, cnt);
                 cnt = group_sum<G>(cnt, red32);
-                if (valid && lg == 0) P.crpt[row] = cnt;
+                if (valid && lg == 0) {
+                    P.crpt[row] = cnt;
+                    tile_sum += cnt;
+                }
             } else {
                 if (valid) ok = coherent ? batch_row<G, T, true, true>(P, row, tk, tv, lg, cnt)
                                          : batch_row<G, T, true, false>(P, row, tk, tv, lg, cnt);
@@ -288,8 +328,8 @@ batch_kernel(const BatchProb *probs, const BatchItem *items, int nitems, BatchSt
                     }
                 }
                 if (valid) {
-                    const int64_t base = __ldcg(reinterpret_cast<const long long *>(P.crpt) + row);
-                    const int64_t want = __ldcg(reinterpret_cast<const long long *>(P.crpt) + row + 1) - base;
+                    const int64_t base = offs[row - r0];
+                    const int64_t want = cnts[row - r0];
                     if (want != n || base + n > P.ccap) ok = false;
                     else
                         for (int t = lg; t < n; t += G) {
@@ -302,6 +342,12 @@ batch_kernel(const BatchProb *probs, const BatchItem *items, int nitems, BatchSt
             group_sync<G>();
         }
         if (!ok_all && atomicCAS(&st->err, 0, SPGEMM_ERR_INTERNAL) == 0) st->where = it;
+        if (I.type == 0) {
+            // the tile's n_nz for the product's scan
+            long long tot;
+            (void)block_excl_scan_ll<kBatchBlock>(tile_sum, tot, red64);
+            if (threadIdx.x == 0) P.tsum[I.tile] = tot;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();

@@ -128,9 +128,11 @@ struct BatchProb {
     int32_t dep;        // product whose C is this B, -1 when B is an input
     int32_t tiny;       // 1: every row has at most kBatchTiny products (one thread per row)
     int32_t pad;
+    long long *tsum;    // per row tile: n_nz sum (symbolic tiles), then its exclusive prefix (scan)
 };
 
 constexpr int kBatchTiny = 8;
+constexpr int kBatchMaxTile = 1024;   // rows per work item, at most
 
 struct BatchItem {
     int32_t type;       // 0 symbolic tile, 1 scan, 2 numeric tile

@@ -90,6 +90,14 @@ def test_each_kernel_variant(variant, tiny):
                 assert np.array_equal(col, want[1]) and np.array_equal(val, want[2])
 
 
+def test_tile_rows_limit():
+    A = W.random_csr(100, 50, 0.1, seed=3)
+    B = W.random_csr(50, 40, 0.1, seed=4)
+    with ops.Handle() as h:
+        with pytest.raises(ops.SpgemmError):
+            Batch(h, [ops.CSR.from_workload(A)], [ops.CSR.from_workload(B)], tile_rows=2048)
+
+
 def test_rows_too_large_are_rejected():
     A = W.random_csr(10, 400, 0.9, seed=1)
     B = W.random_csr(400, 300, 0.5, seed=2)
@@ -100,15 +108,15 @@ def test_rows_too_large_are_rejected():
 
 
 def test_bounded_wait_reports_timeout():
-    # One large product computed by a single work item, followed by a product
-    # that depends on it: the dependent item is taken while the large one is
-    # still running, and a wait limit of one poll runs out.
+    # A large product (108 row tiles of 1024 rows) and a product that depends
+    # on it: its scan item is taken while the tiles are still running, and a
+    # wait limit of one poll runs out.
     big = W.laplacian_3d_7pt(48)
     P = W.aggregation_prolongator(48)
     PT = W.transpose(P)
     with ops.Handle() as h:
         dA, dP, dPT = (ops.CSR.from_workload(m) for m in (big, P, PT))
-        with Batch(h, [dA, dPT], [dP, None], [-1, 0], tile_rows=big.rows, spin_limit=1) as b:
+        with Batch(h, [dA, dPT], [dP, None], [-1, 0], tile_rows=1024, spin_limit=1) as b:
             b.run()
             with pytest.raises(ops.SpgemmError) as e:
                 b.sync()
