@@ -1507,7 +1507,8 @@ int spgemm_batch_create(spgemm_batch **out, spgemm_handle *h, int n, const spgem
         P.tsum = reinterpret_cast<long long *>(b->arena + off_tsum[i]);
         P.ntiles = static_cast<int32_t>((P.M + b->tile_rows - 1) / b->tile_rows);
         P.dep = dep;
-        P.tiny = pmax[i] <= kBatchTiny && !(opt && opt->no_tiny) ? 1 : 0;
+        // 1: every row fits the one-thread path; 0: rows try it first; -1: never
+        P.tiny = (opt && opt->no_tiny) ? -1 : (pmax[i] <= kBatchTiny ? 1 : 0);
         P.pad = 0;
         if (dep < 0) {
             P.brpt = B[i].rpt; P.b64 = B[i].rpt_is_i64 ? 1 : 0; P.bcol = B[i].col; P.bval = B[i].val;

@@ -106,21 +106,28 @@ __device__ __forceinline__ bool batch_row(const BatchProb &P, int64_t row, int *
     return ok;
 }
 
-// Rows of a product with at most kBatchTiny products each (P.tiny): one
-// thread per row keeps the row's distinct columns sorted in kBatchTiny
-// shared slots of its own (slot j of thread t at j * kBatchBlock + t, so the
-// threads of a warp hit distinct banks), adding equal columns in product
-// order; the row is then stored as it stands, without condense or sort.
+// One thread per row: the thread keeps the row's distinct columns sorted
+// in kBatchTiny shared slots of its own (slot j of thread t at
+// j * kBatchBlock + t, so the threads of a warp hit distinct banks), adding
+// equal columns in product order; the row is then stored as it stands,
+// without condense or sort. Rows that do not fit (symbolic: a distinct
+// column past kBatchTiny; numeric: a known size past kBatchTiny) are
+// appended to `over` (tile-local row numbers) for the hash-table path.
 template <bool NUMERIC, bool COHERENT>
 __device__ __forceinline__ bool tiny_rows(const BatchProb &P, int64_t r0, int64_t r1, int *keys,
                                           double *vals, const long long *offs, const int *cnts,
-                                          long long &tile_sum) {
+                                          long long &tile_sum, int *over, int *nover) {
     bool ok = true;
     const int t = threadIdx.x;
     for (int64_t row = r0 + t; row < r1; row += kBatchBlock) {
+        if (NUMERIC && cnts[row - r0] > kBatchTiny) {
+            over[atomicAdd(nover, 1)] = static_cast<int>(row - r0);
+            continue;
+        }
         int n = 0;
+        bool full = false;
         const int64_t p0 = ld_rpt(P.arpt, P.a64, row), p1 = ld_rpt(P.arpt, P.a64, row + 1);
-        for (int64_t p = p0; p < p1; ++p) {
+        for (int64_t p = p0; p < p1 && !full; ++p) {
             const int k = __ldg(P.acol + p);
             const double a = NUMERIC ? __ldg(P.aval + p) : 0.0;
             const int64_t q1 = bload_rpt<COHERENT>(P.brpt, P.b64, k + 1);
@@ -133,9 +140,9 @@ __device__ __forceinline__ bool tiny_rows(const BatchProb &P, int64_t r0, int64_
                     if (NUMERIC) vals[pos * kBatchBlock + t] += v;
                     continue;
                 }
-                if (n == kBatchTiny) {   // more than the bound: cannot happen
-                    ok = false;
-                    continue;
+                if (n == kBatchTiny) {   // a ninth distinct column: the row goes to the tables
+                    full = true;
+                    break;
                 }
                 for (int m = n; m > pos; --m) {
                     keys[m * kBatchBlock + t] = keys[(m - 1) * kBatchBlock + t];
@@ -145,6 +152,11 @@ __device__ __forceinline__ bool tiny_rows(const BatchProb &P, int64_t r0, int64_
                 if (NUMERIC) vals[pos * kBatchBlock + t] = v;
                 ++n;
             }
+        }
+        if (full) {
+            if (NUMERIC) ok = false;   // its size said it fits: cannot happen
+            else over[atomicAdd(nover, 1)] = static_cast<int>(row - r0);
+            continue;
         }
         if (!NUMERIC) {
             P.crpt[row] = n;
@@ -175,6 +187,8 @@ batch_kernel(const BatchProb *probs, const BatchItem *items, int nitems, BatchSt
     __shared__ double vals_all[RG * T];
     __shared__ long long offs[kBatchMaxTile];   // numeric tile: offset of each row in C
     __shared__ int cnts[kBatchMaxTile];         // numeric tile: size of each row
+    __shared__ int over[kBatchMaxTile];         // rows left to the hash tables
+    __shared__ int nover;
     __shared__ int red32[33];
     __shared__ long long red64[33];   // block scan: one slot per warp + the total
     __shared__ int s_item;
@@ -259,17 +273,30 @@ batch_kernel(const BatchProb *probs, const BatchItem *items, int nitems, BatchSt
             }
             __syncthreads();
         }
-        if (P.tiny) {
+        // pass A: one thread per row; rows that do not fit are listed for pass B
+        if (threadIdx.x == 0) nover = 0;
+        __syncthreads();
+        if (P.tiny >= 0) {
             if (I.type == 0)
-                ok_all = coherent ? tiny_rows<false, true>(P, r0, r1, keys_all, vals_all, offs, cnts, tile_sum)
-                                  : tiny_rows<false, false>(P, r0, r1, keys_all, vals_all, offs, cnts, tile_sum);
+                ok_all = coherent ? tiny_rows<false, true>(P, r0, r1, keys_all, vals_all, offs, cnts, tile_sum,
+                                                           over, &nover)
+                                  : tiny_rows<false, false>(P, r0, r1, keys_all, vals_all, offs, cnts, tile_sum,
+                                                            over, &nover);
             else
-                ok_all = coherent ? tiny_rows<true, true>(P, r0, r1, keys_all, vals_all, offs, cnts, tile_sum)
-                                  : tiny_rows<true, false>(P, r0, r1, keys_all, vals_all, offs, cnts, tile_sum);
+                ok_all = coherent ? tiny_rows<true, true>(P, r0, r1, keys_all, vals_all, offs, cnts, tile_sum,
+                                                          over, &nover)
+                                  : tiny_rows<true, false>(P, r0, r1, keys_all, vals_all, offs, cnts, tile_sum,
+                                                           over, &nover);
+        } else {
+            for (int i = threadIdx.x; i < r1 - r0; i += kBatchBlock) over[i] = i;
+            if (threadIdx.x == 0) nover = static_cast<int>(r1 - r0);
         }
-        for (int64_t rb = P.tiny ? r1 : r0; rb < r1; rb += RG) {
-            const int64_t row = rb + g;
-            const bool valid = row < r1;
+        __syncthreads();
+        // pass B: the listed rows, a group of G lanes and a T-slot table each
+        const int n_over = nover;
+        for (int ob = 0; ob < n_over; ob += RG) {
+            const bool valid = ob + g < n_over;
+            const int64_t row = valid ? r0 + over[ob + g] : r0;
             for (int s = lg; s < T; s += G) {
                 tk[s] = -1;
                 tv[s] = 0.0;

@@ -126,7 +126,8 @@ struct BatchProb {
     int64_t *crpt; int32_t *ccol; double *cval; int64_t ccap;
     int32_t ntiles;
     int32_t dep;        // product whose C is this B, -1 when B is an input
-    int32_t tiny;       // 1: every row has at most kBatchTiny products (one thread per row)
+    int32_t tiny;       // 1: every row has at most kBatchTiny products; 0: rows try one thread
+                        // per row first (kBatchTiny distinct columns); -1: hash tables only
     int32_t pad;
     long long *tsum;    // per row tile: n_nz sum (symbolic tiles), then its exclusive prefix (scan)
 };
