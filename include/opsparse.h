@@ -241,7 +241,14 @@ int spgemm_kernel_info(int phase, int id, int32_t *threads_per_row,
  * output row i (of M = A.rows): log1p(nnz of A row i), log1p(n_prod_i),
  * log1p of the max / mean / min length of the referenced B rows (0 for an
  * empty A row) and log((i + 1) / M). The output approximates log1p(n_nz);
- * the predicted size is max(1, ceil(expm1(y) * (1 + margin))). */
+ * the predicted size is max(1, ceil(expm1(y) * (1 + margin) * f)). The
+ * factor f (1, 2, 4, 8 or 16; 1 after spgemm_set_predictor) is the handle's
+ * load feedback, set by each learned-mode spgemm_symbolic for the next one:
+ * doubled when more than a quarter of the rows it tried in one phase
+ * overflowed their table or filled it more than 3/4, halved when at least
+ * 15/16 of them filled it at most 3/8 (numeric tables are 2x apart, so f
+ * moves rows one table up or down). Results never depend on f; only the
+ * tables the rows use do. */
 #define SPGEMM_MODE_PLAIN   0
 #define SPGEMM_MODE_LEARNED 1
 
@@ -255,9 +262,11 @@ int spgemm_set_predictor(spgemm_handle *h, const float *theta, float margin);
  * spgemm_symbolic and spgemm_numeric: SPGEMM_ERR_STATE). */
 int spgemm_set_mode(spgemm_handle *h, int mode);
 
-/* After a learned-mode spgemm_symbolic: rows multiplied in one phase, rows
- * mispredicted (recomputed exactly), rows past the hash bins (exact), and
- * entries of temporary memory used. */
+/* After a learned-mode spgemm_symbolic (up to 7 values): rows multiplied in
+ * one phase, rows mispredicted (recomputed exactly), rows past the hash bins
+ * (exact), entries of temporary memory used, one-phase rows that filled
+ * their table more than 3/4, those that filled it at most 3/8, and the
+ * factor f on the predicted sizes that the call used. */
 int spgemm_learned_stats(const spgemm_handle *h, int64_t *out, int n);
 
 /* Features of rows [row_begin, row_end) of C = A * B into X (device,

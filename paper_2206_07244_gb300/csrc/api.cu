@@ -31,7 +31,9 @@ using namespace ops;
 namespace {
 
 constexpr int kSide = 8;              // side streams for concurrent bin kernels
-constexpr size_t kCountersBytes = 2048;  // 2 x Counters + the error word
+constexpr size_t kCountersBytes = 2048;  // 2 x Counters + the error word + the exact-list count
+static_assert(2 * sizeof(ops::Counters) + 16 <= kCountersBytes, "counter block too small");
+constexpr int kMaxBoost = 16;         // learned sizing: largest factor on the predicted sizes
 
 // Event-timing slots: 0..15 symbolic bins, 16..31 numeric bins, then the
 // setup/binning/scan kernels.
@@ -94,6 +96,7 @@ struct spgemm_handle {
     int mode = 0;                 // SPGEMM_MODE_PLAIN / SPGEMM_MODE_LEARNED
     float *theta = nullptr;       // predictor parameters (device)
     float margin = 0.25f;
+    int lboost = 1;               // factor on the predicted sizes, adapted from call to call
     unsigned char *lscratch = nullptr;
     size_t lscratch_bytes = 0;
     int32_t *tcol = nullptr;      // temporary one-phase rows of the current call
@@ -102,7 +105,8 @@ struct spgemm_handle {
     long long ltotal = 0;
     bool lid = false;
     int64_t xcount = 0;
-    int64_t lstats[4] = {};       // one-phase rows, mispredicted rows, exact rows, temp entries
+    int64_t lstats[7] = {};       // one-phase rows, mispredicted rows, exact rows, temp entries,
+                                  // rows > 3/4 full, rows <= 3/8 full, factor used
     // per-kernel CUDA-event timing (off unless requested)
     // pinned staging for spgemm_multiply_host
     unsigned char *stage = nullptr;
@@ -480,7 +484,9 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
     CK(launch_features(op, mrows, fnp, fmx, fmn, L.X, h->sm_count * 8, s));
     time_end(h, kSlotFeatures, s);
     time_begin(h, kSlotMlp, s);
-    CK(launch_mlp_forward(h->theta, L.X, mw, nullptr, L.pred, h->margin, cap + 1, s));
+    const int boost = h->lboost;
+    const float margin = (1.f + h->margin) * static_cast<float>(boost) - 1.f;
+    CK(launch_mlp_forward(h->theta, L.X, mw, nullptr, L.pred, margin, cap + 1, s));
     const int64_t exact_above = h->cfg.sym_nbins >= 2 ? h->cfg.sym_range[h->cfg.sym_nbins - 2] : -1;
     CK(launch_learned_sizes(crpt, L.pred, mw, exact_above, LLONG_MAX / 4, L.lsizes, s));
     Ranges rn{};
@@ -536,6 +542,7 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
         w.tlimit = total_t;
         w.pred = L.pred; w.xlist = L.xlist; w.xcount = d_xcount(h);
         w.xlimit = mw;
+        w.load = d_counters(h, 0)->load;
         const int slot = kSlotNumBin + j;
         time_begin(h, slot, ss);
         CK(launch_num_onephase(h->cfg.num_kernel[j], op, w, ss));
@@ -579,6 +586,27 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
     h->lstats[0] -= h->lstats[1];
     h->lstats[2] = cnt_last;
     h->lstats[3] = total_t;
+    // Load feedback: the factor on the predicted sizes for the next call.
+    // Tables are 2x apart, so doubling the factor moves a row one table up.
+    // Double it when more than a quarter of the rows tried in one phase
+    // overflowed or ended more than 3/4 full (under-predicted: probes get
+    // long); halve it when at least 15/16 of them ended at most 3/8 full
+    // (the next smaller table would hold them at most 3/4 full).
+    unsigned long long hi = 0, lo = 0;
+    for (int k = 0; k < kLoadSlots; ++k) {
+        hi += h->h_cnt[0].load[k];
+        lo += h->h_cnt[0].load[kLoadSlots + k];
+    }
+    h->lstats[4] = static_cast<int64_t>(hi);
+    h->lstats[5] = static_cast<int64_t>(lo);
+    h->lstats[6] = boost;
+    const long long tried = h->lstats[0] + h->lstats[1];
+    if (tried > 0) {
+        if (4 * (static_cast<long long>(hi) + h->lstats[1]) > tried)
+            h->lboost = std::min(boost * 2, kMaxBoost);
+        else if (boost > 1 && 16 * static_cast<long long>(lo) >= 15 * h->lstats[0])
+            h->lboost = boost / 2;
+    }
     return SPGEMM_OK;
 }
 
@@ -1279,6 +1307,7 @@ int spgemm_set_predictor(spgemm_handle *h, const float *theta, float margin) {
     CK(cudaMemcpyAsync(h->theta, theta, sizeof(float) * (size_t)mlp_param_count(), cudaMemcpyDefault,
                        h->stream));
     h->margin = margin;
+    h->lboost = 1;
     return SPGEMM_OK;
 }
 
@@ -1292,7 +1321,7 @@ int spgemm_set_mode(spgemm_handle *h, int mode) {
 
 int spgemm_learned_stats(const spgemm_handle *h, int64_t *out, int n) {
     if (!h || !out || n < 0) return SPGEMM_ERR_INVALID;
-    for (int i = 0; i < std::min(n, 4); ++i) out[i] = h->lstats[i];
+    for (int i = 0; i < std::min(n, 7); ++i) out[i] = h->lstats[i];
     return SPGEMM_OK;
 }
 

@@ -8,6 +8,7 @@
 namespace ops {
 
 constexpr int kMaxBins = 16;
+constexpr int kLoadSlots = 16;
 
 // Operands of one SpGEMM row window, as the kernels see them.
 struct Operands {
@@ -43,6 +44,7 @@ struct BinWork {
     int32_t *xlist;       // rows for the exact path (overflowed rows are appended)
     unsigned long long *xcount;
     long long xlimit;     // entries of xlist (bounds check)
+    unsigned long long *load;   // table loads of the one-phase rows (Counters::load), or nullptr
 };
 
 struct Ranges {
@@ -59,6 +61,11 @@ struct Counters {
     unsigned long long max_size;
     unsigned long long total;
     unsigned long long flags;         // bit 0: some row of B has decreasing columns
+    // one-phase (learned sizing) rows by the load their table ended with,
+    // spread over kLoadSlots counters each (by block) against contention:
+    // [0, kLoadSlots) more than 3/4 full, [kLoadSlots, 2 kLoadSlots) at
+    // most 3/8 full (the next smaller table would hold them at most 3/4 full)
+    unsigned long long load[2 * kLoadSlots];
 };
 
 // Windowed pass 2 of the numeric bitmap kernel: at most kWinMaxLists A

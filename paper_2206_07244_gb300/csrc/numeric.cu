@@ -218,7 +218,11 @@ num_hash_kernel(Operands op, BinWork w) {
             return;   // uniform over the row group
         }
         n_expect = n;
-        if (valid && lg == 0) w.crpt[row] = n;
+        if (valid && lg == 0) {
+            w.crpt[row] = n;
+            if (w.load && 4 * n > 3 * T) atomicAdd(w.load + blockIdx.x % kLoadSlots, 1ull);
+            else if (w.load && 8 * n <= 3 * T) atomicAdd(w.load + kLoadSlots + blockIdx.x % kLoadSlots, 1ull);
+        }
     } else {
         if (valid && n != n_expect) set_error(w.err, DERR_COUNT_MISMATCH);
         if (P > T) {  // cannot happen within the kernel's capacity; never index past the table

@@ -226,3 +226,59 @@ def test_trained_network_gain():
           f"learned/plain speedup {t_plain / t_learned:.3f}, stats {st}")
     assert st["one_phase_rows"] > 0.9 * A.rows
     assert t_learned < 0.9 * t_bound
+
+
+def test_load_feedback_factor():
+    # A network that predicts size 1 for every row: the first call's one-phase
+    # rows all overflow, so each later call doubles the factor on the
+    # predicted sizes (up to 16); a new predictor starts again at 1. Every
+    # call's C equals the oracle's whatever the factor.
+    A = W.stencil27(12, seed=51)
+    dA = dev(A)
+    rpt, col, val, ab = oracle.spgemm(A, A)
+    theta = np.zeros(omlp.N_PARAMS, dtype=np.float32)
+    factors = []
+    with ops.Handle() as h:
+        h.set_predictor(theta, 0.0)
+        h.set_mode("learned")
+        for _ in range(6):
+            C = h.multiply(dA, dA)
+            h.status()
+            st = h.learned_stats()
+            factors.append(st["size_factor"])
+            got = C.numpy()
+            assert np.array_equal(got[0], rpt) and np.array_equal(got[1], col)
+            assert_values_close(got[2], val, ab)
+        assert factors == [1, 2, 4, 8, 16, 16]
+        h.set_predictor(theta, 0.0)
+        h.multiply(dA, dA)
+        assert h.learned_stats()["size_factor"] == 1
+
+
+def test_load_feedback_settles_on_stencil():
+    # The committed network under-predicts stencil rows about 2x (a banded
+    # matrix with the same features has half the entries); the feedback
+    # moves them one table up and then holds the factor.
+    if not os.path.exists(learned.WEIGHTS):
+        pytest.skip("no trained weights")
+    theta = np.load(learned.WEIGHTS)
+    margin = json.load(open(learned.MANIFEST))["margin"]
+    A = W.stencil27(24, seed=52)
+    dA = dev(A)
+    rpt, col, val, ab = oracle.spgemm(A, A)
+    with ops.Handle() as h:
+        h.set_predictor(theta, margin)
+        h.set_mode("learned")
+        stats = []
+        for _ in range(4):
+            C = h.multiply(dA, dA)
+            h.status()
+            stats.append(h.learned_stats())
+            got = C.numpy()
+            assert np.array_equal(got[0], rpt) and np.array_equal(got[1], col)
+            assert_values_close(got[2], val, ab)
+    print([(s["size_factor"], s["rows_over_3_4_full"], s["one_phase_rows"]) for s in stats])
+    last = stats[-1]
+    assert last["size_factor"] == stats[-2]["size_factor"]
+    assert last["rows_over_3_4_full"] + last["mispredicted_rows"] <= 0.25 * (
+        last["one_phase_rows"] + last["mispredicted_rows"])
