@@ -241,14 +241,16 @@ int spgemm_kernel_info(int phase, int id, int32_t *threads_per_row,
  * output row i (of M = A.rows): log1p(nnz of A row i), log1p(n_prod_i),
  * log1p of the max / mean / min length of the referenced B rows (0 for an
  * empty A row) and log((i + 1) / M). The output approximates log1p(n_nz);
- * the predicted size is max(1, ceil(expm1(y) * (1 + margin) * f)). The
- * factor f (1, 2, 4, 8 or 16; 1 after spgemm_set_predictor) is the handle's
- * load feedback, set by each learned-mode spgemm_symbolic for the next one:
- * doubled when more than a quarter of the rows it tried in one phase
- * overflowed their table or filled it more than 3/4, halved when at least
- * 15/16 of them filled it at most 3/8 (numeric tables are 2x apart, so f
- * moves rows one table up or down). Results never depend on f; only the
- * tables the rows use do. */
+ * the predicted size is p = max(1, ceil(expm1(y) * (1 + margin))). Rows are
+ * put in classes by p (class j: the numeric bin that p falls in) and the
+ * size used is ceil(p * 2^k_j), at least 1 and at most the row's n_prod.
+ * The exponents k_j (|k_j| <= 4; 0 after spgemm_set_predictor) are the
+ * handle's load feedback, updated by each learned-mode spgemm_symbolic for
+ * the next one: k_j + 1 when more than a quarter of class j's rows tried in
+ * one phase overflowed their table or filled it more than 3/4, k_j - 1 when
+ * at least 15/16 of them would fill the next smaller table at most 3/4
+ * (a factor of 2 moves a row at most one table). Results never depend on
+ * the k_j; only the tables the rows use do. */
 #define SPGEMM_MODE_PLAIN   0
 #define SPGEMM_MODE_LEARNED 1
 
@@ -262,11 +264,12 @@ int spgemm_set_predictor(spgemm_handle *h, const float *theta, float margin);
  * spgemm_symbolic and spgemm_numeric: SPGEMM_ERR_STATE). */
 int spgemm_set_mode(spgemm_handle *h, int mode);
 
-/* After a learned-mode spgemm_symbolic (up to 7 values): rows multiplied in
- * one phase, rows mispredicted (recomputed exactly), rows past the hash bins
- * (exact), entries of temporary memory used, one-phase rows that filled
- * their table more than 3/4, those that filled it at most 3/8, and the
- * factor f on the predicted sizes that the call used. */
+/* After a learned-mode spgemm_symbolic (up to 6 + SPGEMM_MAX_BINS values):
+ * rows multiplied in one phase, rows mispredicted (recomputed exactly), rows
+ * past the hash bins (exact), entries of temporary memory used, one-phase
+ * rows that filled their table more than 3/4, those that the next smaller
+ * table would hold at most 3/4 full, then the factor exponent k_j that the
+ * call used for each class j. */
 int spgemm_learned_stats(const spgemm_handle *h, int64_t *out, int n);
 
 /* Features of rows [row_begin, row_end) of C = A * B into X (device,

@@ -211,11 +211,12 @@ class Handle:
         _abi.check(self._lib.spgemm_set_mode(self._h, m), "spgemm_set_mode")
 
     def learned_stats(self) -> dict:
-        arr = (ctypes.c_int64 * 7)()
-        _abi.check(self._lib.spgemm_learned_stats(self._h, arr, 7), "spgemm_learned_stats")
+        n = 6 + MAX_BINS
+        arr = (ctypes.c_int64 * n)()
+        _abi.check(self._lib.spgemm_learned_stats(self._h, arr, n), "spgemm_learned_stats")
         return {"one_phase_rows": arr[0], "mispredicted_rows": arr[1], "exact_rows": arr[2],
-                "temp_entries": arr[3], "rows_over_3_4_full": arr[4], "rows_under_3_8_full": arr[5],
-                "size_factor": arr[6]}
+                "temp_entries": arr[3], "rows_over_3_4_full": arr[4],
+                "rows_fit_smaller_table": arr[5], "factor_log2": list(arr[6:n])}
 
     # -- diagnostics -------------------------------------------------------------
     def stats(self) -> dict:

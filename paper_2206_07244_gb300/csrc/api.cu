@@ -33,7 +33,6 @@ namespace {
 constexpr int kSide = 8;              // side streams for concurrent bin kernels
 constexpr size_t kCountersBytes = 2048;  // 2 x Counters + the error word + the exact-list count
 static_assert(2 * sizeof(ops::Counters) + 16 <= kCountersBytes, "counter block too small");
-constexpr int kMaxBoost = 16;         // learned sizing: largest factor on the predicted sizes
 
 // Event-timing slots: 0..15 symbolic bins, 16..31 numeric bins, then the
 // setup/binning/scan kernels.
@@ -96,7 +95,8 @@ struct spgemm_handle {
     int mode = 0;                 // SPGEMM_MODE_PLAIN / SPGEMM_MODE_LEARNED
     float *theta = nullptr;       // predictor parameters (device)
     float margin = 0.25f;
-    int lboost = 1;               // factor on the predicted sizes, adapted from call to call
+    int lfk[kMaxBins] = {};       // per class: exponent of the factor on the predicted sizes,
+                                  // adapted from call to call (load feedback)
     unsigned char *lscratch = nullptr;
     size_t lscratch_bytes = 0;
     int32_t *tcol = nullptr;      // temporary one-phase rows of the current call
@@ -105,8 +105,9 @@ struct spgemm_handle {
     long long ltotal = 0;
     bool lid = false;
     int64_t xcount = 0;
-    int64_t lstats[7] = {};       // one-phase rows, mispredicted rows, exact rows, temp entries,
-                                  // rows > 3/4 full, rows <= 3/8 full, factor used
+    int64_t lstats[6 + kMaxBins] = {};  // one-phase rows, mispredicted rows, exact rows, temp
+                                        // entries, rows > 3/4 full, rows that fit the next
+                                        // smaller table, factor exponents used per class
     // per-kernel CUDA-event timing (off unless requested)
     // pinned staging for spgemm_multiply_host
     unsigned char *stage = nullptr;
@@ -212,6 +213,8 @@ struct LScratch {
     long long *pred;
     int64_t *lsizes;
     int32_t *xlist;
+    uint8_t *cls;         // class of each row (bin of its prediction)
+    unsigned long long *fb;   // load feedback counters (kFbCounters)
     unsigned char *fws;   // n_prod (8 B) + max (4 B) + min (4 B) per row
 };
 
@@ -223,13 +226,16 @@ LScratch lscratch_layout(spgemm_handle *h, int64_t mw) {
     L.pred = reinterpret_cast<long long *>(p);          p += align256(sizeof(long long) * m);
     L.lsizes = reinterpret_cast<int64_t *>(p);          p += align256(sizeof(int64_t) * m);
     L.xlist = reinterpret_cast<int32_t *>(p);           p += align256(sizeof(int32_t) * m);
+    L.cls = reinterpret_cast<uint8_t *>(p);             p += align256(m);
+    L.fb = reinterpret_cast<unsigned long long *>(p);   p += align256(sizeof(unsigned long long) * kFbCounters);
     L.fws = p;
     return L;
 }
 
 int ensure_lscratch(spgemm_handle *h, int64_t mw) {
     const size_t m = (size_t)std::max<int64_t>(mw, 1);
-    const size_t need = align256(24 * m) + 2 * align256(8 * m) + align256(4 * m) + align256(16 * m) + 256;
+    const size_t need = align256(24 * m) + 2 * align256(8 * m) + align256(4 * m) + align256(m) +
+                        align256(sizeof(unsigned long long) * kFbCounters) + align256(16 * m) + 256;
     if (h->lscratch && h->lscratch_bytes >= need) return SPGEMM_OK;
     if (h->lscratch) {
         if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SPGEMM_ERR_CUDA;
@@ -484,11 +490,16 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
     CK(launch_features(op, mrows, fnp, fmx, fmn, L.X, h->sm_count * 8, s));
     time_end(h, kSlotFeatures, s);
     time_begin(h, kSlotMlp, s);
-    const int boost = h->lboost;
-    const float margin = (1.f + h->margin) * static_cast<float>(boost) - 1.f;
-    CK(launch_mlp_forward(h->theta, L.X, mw, nullptr, L.pred, margin, cap + 1, s));
+    CK(launch_mlp_forward(h->theta, L.X, mw, nullptr, L.pred, h->margin, cap + 1, s));
     const int64_t exact_above = h->cfg.sym_nbins >= 2 ? h->cfg.sym_range[h->cfg.sym_nbins - 2] : -1;
-    CK(launch_learned_sizes(crpt, L.pred, mw, exact_above, LLONG_MAX / 4, L.lsizes, s));
+    SizeFactors sf{};
+    sf.nb = nb;
+    for (int j = 0; j < nb; ++j) {
+        sf.lim[j] = h->cfg.num_range[j];
+        sf.k[j] = h->lfk[j];
+    }
+    CK(cudaMemsetAsync(L.fb, 0, sizeof(unsigned long long) * kFbCounters, s));
+    CK(launch_learned_sizes(crpt, L.pred, mw, exact_above, LLONG_MAX / 4, L.lsizes, sf, L.cls, L.fb, s));
     Ranges rn{};
     rn.nb = nb;
     for (int j = 0; j < nb; ++j) rn.r[j] = h->cfg.num_range[j];
@@ -542,7 +553,9 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
         w.tlimit = total_t;
         w.pred = L.pred; w.xlist = L.xlist; w.xcount = d_xcount(h);
         w.xlimit = mw;
-        w.load = d_counters(h, 0)->load;
+        w.lcls = L.cls;
+        w.fb = L.fb;
+        w.tprev = j > 0 ? num_kernel(h->cfg.num_kernel[j - 1]).table : 0;
         const int slot = kSlotNumBin + j;
         time_begin(h, slot, ss);
         CK(launch_num_onephase(h->cfg.num_kernel[j], op, w, ss));
@@ -578,6 +591,9 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
     time_begin(h, kSlotNumPass1, s);
     CK(launch_bin_pass1(crpt, mw, all, op, d_counters(h, 1), d_tiles(h), s));
     time_end(h, kSlotNumPass1, s);
+    unsigned long long *h_fb = reinterpret_cast<unsigned long long *>(
+        reinterpret_cast<unsigned char *>(h->h_cnt) + 2 * sizeof(Counters) + 64);
+    CK(cudaMemcpyAsync(h_fb, L.fb, sizeof(unsigned long long) * kFbCounters, cudaMemcpyDeviceToHost, s));
     if ((rc = read_counters(h))) return rc;
     *nnz_out = static_cast<int64_t>(h->h_cnt[1].total);
     h->lstats[0] = 0;
@@ -586,26 +602,28 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
     h->lstats[0] -= h->lstats[1];
     h->lstats[2] = cnt_last;
     h->lstats[3] = total_t;
-    // Load feedback: the factor on the predicted sizes for the next call.
-    // Tables are 2x apart, so doubling the factor moves a row one table up.
-    // Double it when more than a quarter of the rows tried in one phase
-    // overflowed or ended more than 3/4 full (under-predicted: probes get
-    // long); halve it when at least 15/16 of them ended at most 3/8 full
-    // (the next smaller table would hold them at most 3/4 full).
-    unsigned long long hi = 0, lo = 0;
-    for (int k = 0; k < kLoadSlots; ++k) {
-        hi += h->h_cnt[0].load[k];
-        lo += h->h_cnt[0].load[kLoadSlots + k];
-    }
-    h->lstats[4] = static_cast<int64_t>(hi);
-    h->lstats[5] = static_cast<int64_t>(lo);
-    h->lstats[6] = boost;
-    const long long tried = h->lstats[0] + h->lstats[1];
-    if (tried > 0) {
-        if (4 * (static_cast<long long>(hi) + h->lstats[1]) > tried)
-            h->lboost = std::min(boost * 2, kMaxBoost);
-        else if (boost > 1 && 16 * static_cast<long long>(lo) >= 15 * h->lstats[0])
-            h->lboost = boost / 2;
+    // Load feedback, per class of rows: the factor for the next call.
+    // Doubling a class's factor moves its rows at most one table up, halving
+    // it at most one table down. Double it when more than a quarter of the
+    // class's rows tried in one phase overflowed or ended more than 3/4 full
+    // (under-predicted: probes get long); halve it when at least 15/16 of
+    // them would fill the next smaller table at most 3/4 (over-predicted:
+    // set-up, condense and sort scan a table larger than needed).
+    auto fbsum = [&](int grp, int b) {
+        unsigned long long t = 0;
+        for (int k = 0; k < kLoadSlots; ++k) t += h_fb[(grp * kMaxBins + b) * kLoadSlots + k];
+        return static_cast<long long>(t);
+    };
+    h->lstats[4] = 0;
+    h->lstats[5] = 0;
+    for (int b = 0; b < kMaxBins; ++b) h->lstats[6 + b] = h->lfk[b];
+    for (int b = 0; b + 1 < nb; ++b) {
+        const long long tried = fbsum(0, b), hi = fbsum(1, b), lo = fbsum(2, b), mis = fbsum(3, b);
+        h->lstats[4] += hi;
+        h->lstats[5] += lo;
+        if (tried <= 0) continue;
+        if (4 * (hi + mis) > tried) h->lfk[b] = std::min(h->lfk[b] + 1, kMaxFactorLog2);
+        else if (16 * lo >= 15 * tried) h->lfk[b] = std::max(h->lfk[b] - 1, -kMaxFactorLog2);
     }
     return SPGEMM_OK;
 }
@@ -727,7 +745,8 @@ int spgemm_create(spgemm_handle **out, const spgemm_config *cfg, spgemm_alloc_fn
         }
         if (rc) break;
         if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess) { rc = SPGEMM_ERR_CUDA; break; }
-        if (cudaMallocHost(&h->h_cnt, 2 * sizeof(Counters) + 64) != cudaSuccess) { rc = SPGEMM_ERR_OOM; break; }
+        if (cudaMallocHost(&h->h_cnt, 2 * sizeof(Counters) + 64 + sizeof(unsigned long long) * kFbCounters) !=
+            cudaSuccess) { rc = SPGEMM_ERR_OOM; break; }
         if (!alloc) {
             cudaMemPoolProps props{};
             props.allocType = cudaMemAllocationTypePinned;
@@ -1307,7 +1326,7 @@ int spgemm_set_predictor(spgemm_handle *h, const float *theta, float margin) {
     CK(cudaMemcpyAsync(h->theta, theta, sizeof(float) * (size_t)mlp_param_count(), cudaMemcpyDefault,
                        h->stream));
     h->margin = margin;
-    h->lboost = 1;
+    for (int &k : h->lfk) k = 0;
     return SPGEMM_OK;
 }
 
@@ -1321,7 +1340,7 @@ int spgemm_set_mode(spgemm_handle *h, int mode) {
 
 int spgemm_learned_stats(const spgemm_handle *h, int64_t *out, int n) {
     if (!h || !out || n < 0) return SPGEMM_ERR_INVALID;
-    for (int i = 0; i < std::min(n, 7); ++i) out[i] = h->lstats[i];
+    for (int i = 0; i < std::min(n, 6 + kMaxBins); ++i) out[i] = h->lstats[i];
     return SPGEMM_OK;
 }
 

@@ -8,7 +8,24 @@
 namespace ops {
 
 constexpr int kMaxBins = 16;
-constexpr int kLoadSlots = 16;
+
+// Learned sizing, load feedback: each class of rows (the numeric bin of a
+// row's predicted size) has a factor 2^k on its predicted sizes,
+// |k| <= kMaxFactorLog2. The one-phase kernels count, per class, the rows
+// tried (group 0), those that ended more than 3/4 full (1), those that the
+// next smaller table would hold at most 3/4 full (2) and the mispredicted
+// ones (3), each spread over kLoadSlots counters (by block) against
+// contention: counter (group * kMaxBins + class) * kLoadSlots + slot.
+constexpr int kMaxFactorLog2 = 4;
+constexpr int kLoadSlots = 8;
+constexpr int kFbGroups = 4;
+constexpr int kFbCounters = kFbGroups * kMaxBins * kLoadSlots;
+
+struct SizeFactors {
+    long long lim[kMaxBins];   // class j: sizes in (lim[j-1], lim[j]]; the last class takes the rest
+    int k[kMaxBins];           // exponent of each class's factor
+    int nb;
+};
 
 // Operands of one SpGEMM row window, as the kernels see them.
 struct Operands {
@@ -44,7 +61,9 @@ struct BinWork {
     int32_t *xlist;       // rows for the exact path (overflowed rows are appended)
     unsigned long long *xcount;
     long long xlimit;     // entries of xlist (bounds check)
-    unsigned long long *load;   // table loads of the one-phase rows (Counters::load), or nullptr
+    const uint8_t *lcls;  // class of each window row (the bin of its prediction)
+    unsigned long long *fb;   // load feedback counters (kFbCounters), or nullptr
+    long long tprev;      // slots of the next smaller table (0: none)
 };
 
 struct Ranges {
@@ -61,11 +80,6 @@ struct Counters {
     unsigned long long max_size;
     unsigned long long total;
     unsigned long long flags;         // bit 0: some row of B has decreasing columns
-    // one-phase (learned sizing) rows by the load their table ended with,
-    // spread over kLoadSlots counters each (by block) against contention:
-    // [0, kLoadSlots) more than 3/4 full, [kLoadSlots, 2 kLoadSlots) at
-    // most 3/8 full (the next smaller table would hold them at most 3/4 full)
-    unsigned long long load[2 * kLoadSlots];
 };
 
 // Windowed pass 2 of the numeric bitmap kernel: at most kWinMaxLists A
@@ -178,6 +192,7 @@ cudaError_t launch_adam(float *theta, const float *grad, float *m, float *v, int
 // sizes[i] = min(pred[i], n_prod[i]), or `huge` when n_prod[i] > exact_above
 cudaError_t launch_learned_sizes(const int64_t *nprod, const long long *pred, int64_t n,
                                  long long exact_above, long long huge, int64_t *sizes,
+                                 const SizeFactors &sf, uint8_t *cls, unsigned long long *fb,
                                  cudaStream_t s);
 // copy one-phase rows from temporary memory into C (rows whose pred is -1 skipped)
 cudaError_t launch_copy_rows(const BinWork &w, cudaStream_t s);

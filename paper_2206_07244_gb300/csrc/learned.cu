@@ -312,21 +312,49 @@ cudaError_t launch_adam(float *theta, const float *grad, float *m, float *v, int
 // Sizes for the learned binning: rows past the symbolic hash bins go to
 // the exact path (a huge size); others get min(prediction, n_prod), since a
 // row never has more distinct keys than products.
-__global__ void learned_sizes_kernel(const int64_t *nprod, const long long *pred, int64_t n,
-                                     long long exact_above, long long huge, int64_t *sizes) {
+// Sizes for the binning by prediction: rows whose n_prod passes exact_above
+// go to the exact path (huge); the others take their class's factor on the
+// predicted size (class = bin of the prediction), at least 1 and at most
+// n_prod (an upper bound of n_nz). Each block counts its rows per class that
+// land in a hash bin (tried in one phase) into the feedback counters.
+__global__ void __launch_bounds__(256)
+learned_sizes_kernel(const int64_t *nprod, const long long *pred, int64_t n, long long exact_above,
+                     long long huge, int64_t *sizes, SizeFactors sf, uint8_t *cls,
+                     unsigned long long *fb) {
+    __shared__ unsigned hist[kMaxBins];
+    if (threadIdx.x < kMaxBins) hist[threadIdx.x] = 0u;
+    __syncthreads();
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const long long np = nprod[i];
-    const long long p = pred[i];
-    sizes[i] = np > exact_above ? huge : (p < np ? p : np);
+    if (i < n) {
+        const long long np = nprod[i];
+        const long long p = pred[i];
+        int b = 0;
+        while (b < sf.nb - 1 && p > sf.lim[b]) ++b;
+        long long sz = huge;
+        if (np <= exact_above) {
+            const int k = sf.k[b];
+            long long q = k >= 0 ? (p << k) : ((p + (1ll << -k) - 1) >> -k);
+            if (q < 1) q = 1;
+            sz = q < np ? q : np;
+            if (b < sf.nb - 1 && sz <= sf.lim[sf.nb - 2]) atomicAdd(&hist[b], 1u);
+        }
+        sizes[i] = sz;
+        cls[i] = static_cast<uint8_t>(b);
+    }
+    __syncthreads();
+    if (fb && threadIdx.x < kMaxBins && hist[threadIdx.x] > 0u)
+        atomicAdd(fb + threadIdx.x * kLoadSlots + blockIdx.x % kLoadSlots,
+                  static_cast<unsigned long long>(hist[threadIdx.x]));
 }
 
 cudaError_t launch_learned_sizes(const int64_t *nprod, const long long *pred, int64_t n,
                                  long long exact_above, long long huge, int64_t *sizes,
+                                 const SizeFactors &sf, uint8_t *cls, unsigned long long *fb,
                                  cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    learned_sizes_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(nprod, pred, n,
-                                                                               exact_above, huge, sizes);
+    if (sf.nb < 1 || sf.nb > kMaxBins) return cudaErrorInvalidValue;
+    learned_sizes_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
+        nprod, pred, n, exact_above, huge, sizes, sf, cls, fb);
     return cudaGetLastError();
 }
 

@@ -211,6 +211,8 @@ num_hash_kernel(Operands op, BinWork w) {
         if (full[g] || P > T) {
             if (valid && lg == 0) {   // C.rpt keeps n_prod for the exact symbolic kernel
                 w.pred[row] = -1;
+                if (w.fb)
+                    atomicAdd(w.fb + (3 * kMaxBins + w.lcls[row]) * kLoadSlots + blockIdx.x % kLoadSlots, 1ull);
                 const unsigned long long at = atomicAdd(w.xcount, 1ull);
                 if (at < static_cast<unsigned long long>(w.xlimit)) w.xlist[at] = static_cast<int32_t>(row);
                 else set_error(w.err, DERR_BOUNDS);
@@ -220,8 +222,10 @@ num_hash_kernel(Operands op, BinWork w) {
         n_expect = n;
         if (valid && lg == 0) {
             w.crpt[row] = n;
-            if (w.load && 4 * n > 3 * T) atomicAdd(w.load + blockIdx.x % kLoadSlots, 1ull);
-            else if (w.load && 8 * n <= 3 * T) atomicAdd(w.load + kLoadSlots + blockIdx.x % kLoadSlots, 1ull);
+            // load feedback: more than 3/4 full, or at most 3/4 of the next smaller table
+            const int grp = 4 * n > 3 * T ? 1 : (w.tprev > 0 && 4ll * n <= 3 * w.tprev ? 2 : 0);
+            if (w.fb && grp)
+                atomicAdd(w.fb + (grp * kMaxBins + w.lcls[row]) * kLoadSlots + blockIdx.x % kLoadSlots, 1ull);
         }
     } else {
         if (valid && n != n_expect) set_error(w.err, DERR_COUNT_MISMATCH);
@@ -711,9 +715,27 @@ __global__ void copy_rows_kernel(BinWork w) {
         if (lane == 0) set_error(w.err, DERR_BOUNDS);
         return;
     }
-    for (int64_t t = lane; t < n; t += 32) {
-        w.ccol[base + t] = scol[t];
-        w.cval[base + t] = sval[t];
+    // four loads in flight per lane before the stores (the temporary rows
+    // are read-only here)
+    for (int64_t t0 = 0; t0 < n; t0 += 128) {
+        int32_t c[4];
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t t = t0 + u * 32 + lane;
+            if (t < n) {
+                c[u] = __ldg(scol + t);
+                v[u] = __ldg(sval + t);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t t = t0 + u * 32 + lane;
+            if (t < n) {
+                w.ccol[base + t] = c[u];
+                w.cval[base + t] = v[u];
+            }
+        }
     }
 }
 

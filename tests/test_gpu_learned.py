@@ -230,14 +230,14 @@ def test_trained_network_gain():
 
 def test_load_feedback_factor():
     # A network that predicts size 1 for every row: the first call's one-phase
-    # rows all overflow, so each later call doubles the factor on the
-    # predicted sizes (up to 16); a new predictor starts again at 1. Every
-    # call's C equals the oracle's whatever the factor.
+    # rows all overflow, so each later call doubles the factor of their class
+    # (class 0, up to 2^4); a new predictor starts again at 1. Every call's C
+    # equals the oracle's whatever the factors.
     A = W.stencil27(12, seed=51)
     dA = dev(A)
     rpt, col, val, ab = oracle.spgemm(A, A)
     theta = np.zeros(omlp.N_PARAMS, dtype=np.float32)
-    factors = []
+    ks = []
     with ops.Handle() as h:
         h.set_predictor(theta, 0.0)
         h.set_mode("learned")
@@ -245,20 +245,45 @@ def test_load_feedback_factor():
             C = h.multiply(dA, dA)
             h.status()
             st = h.learned_stats()
-            factors.append(st["size_factor"])
+            ks.append(st["factor_log2"][0])
+            assert all(k == 0 for k in st["factor_log2"][1:])
             got = C.numpy()
             assert np.array_equal(got[0], rpt) and np.array_equal(got[1], col)
             assert_values_close(got[2], val, ab)
-        assert factors == [1, 2, 4, 8, 16, 16]
+        assert ks == [0, 1, 2, 3, 4, 4]
         h.set_predictor(theta, 0.0)
         h.multiply(dA, dA)
-        assert h.learned_stats()["size_factor"] == 1
+        assert h.learned_stats()["factor_log2"][0] == 0
+
+
+def test_load_feedback_lowers_overpredicted_classes():
+    # y = 6 predicts 403 entries for every row (a 512-slot table, over 2 bins
+    # above what a stencil row of at most 125 entries needs); the feedback
+    # halves that class's factor until the rows use a table they fill
+    # between 3/8 and 3/4... and stays there.
+    A = W.stencil27(16, seed=53)
+    dA = dev(A)
+    theta = np.zeros(omlp.N_PARAMS, dtype=np.float32)
+    theta[-1] = 6.0
+    rpt, col, val, ab = oracle.spgemm(A, A)
+    with ops.Handle() as h:
+        h.set_predictor(theta, 0.0)
+        h.set_mode("learned")
+        ks = []
+        for _ in range(6):
+            C = h.multiply(dA, dA)
+            h.status()
+            ks.append(min(h.learned_stats()["factor_log2"]))
+            got = C.numpy()
+            assert np.array_equal(got[0], rpt) and np.array_equal(got[1], col)
+            assert_values_close(got[2], val, ab)
+    assert ks[0] == 0 and ks[-1] < 0 and ks[-1] == ks[-2]
 
 
 def test_load_feedback_settles_on_stencil():
     # The committed network under-predicts stencil rows about 2x (a banded
     # matrix with the same features has half the entries); the feedback
-    # moves them one table up and then holds the factor.
+    # moves them one table up and then holds the factors.
     if not os.path.exists(learned.WEIGHTS):
         pytest.skip("no trained weights")
     theta = np.load(learned.WEIGHTS)
@@ -270,15 +295,15 @@ def test_load_feedback_settles_on_stencil():
         h.set_predictor(theta, margin)
         h.set_mode("learned")
         stats = []
-        for _ in range(4):
+        for _ in range(6):
             C = h.multiply(dA, dA)
             h.status()
             stats.append(h.learned_stats())
             got = C.numpy()
             assert np.array_equal(got[0], rpt) and np.array_equal(got[1], col)
             assert_values_close(got[2], val, ab)
-    print([(s["size_factor"], s["rows_over_3_4_full"], s["one_phase_rows"]) for s in stats])
+    print([(s["factor_log2"][:6], s["rows_over_3_4_full"], s["one_phase_rows"]) for s in stats])
     last = stats[-1]
-    assert last["size_factor"] == stats[-2]["size_factor"]
+    assert last["factor_log2"] == stats[-2]["factor_log2"]
     assert last["rows_over_3_4_full"] + last["mispredicted_rows"] <= 0.25 * (
         last["one_phase_rows"] + last["mispredicted_rows"])
