@@ -584,20 +584,23 @@ def main():
         if args.save_config:
             json.dump(best, open(args.save_config, "w"))
 
+    # the device-resident handle and the C blocks cached by torch are given
+    # back before the other legs, which start from a clean allocator, as a
+    # fresh process would
+    h.close()
+    del dA
+    torch.cuda.empty_cache()
+
     e2e = None
     if not args.no_e2e and rank == 0:
         e2e = run_e2e(A, lib, args.e2e_steps, nprod_slab if ws == 1 else None)
+        torch.cuda.empty_cache()
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and ws == 1:
         cpu = cpu_baseline(A)
 
     learned_legs = batched = None
-    legs = (args.learned or args.batched) and rank == 0
-    if legs:
-        h.close()
-        del dA
-        torch.cuda.empty_cache()
     if args.batched and rank == 0:
         batched = batched_eval()
         torch.cuda.empty_cache()
@@ -632,8 +635,6 @@ def main():
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
-    if not legs:
-        h.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
