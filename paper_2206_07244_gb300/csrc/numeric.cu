@@ -639,7 +639,6 @@ static const struct { int block, iters; BmFn fn; } g_num_bm[] = {
     {1024, 4, &num_bitmap_kernel<1024, 4>}, {1024, 8, &num_bitmap_kernel<1024, 8>},
     {512, 4, &num_bitmap_kernel<512, 4>},   {256, 4, &num_bitmap_kernel<256, 4>},
 };
-static int g_smem_optin = 0;
 
 int num_kernel_count() { return kNumHash + 1; }
 
@@ -663,7 +662,6 @@ cudaError_t num_prepare(int smem_optin) {
         if (e != cudaSuccess) return e;
     }
     g_num_bitmap.table = static_cast<long long>((smem_optin - sizeof(WalkScratch)) / 12) * 64;
-    g_smem_optin = smem_optin;
     for (const auto &v : g_num_bm) {
         cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(v.fn),
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
