@@ -173,6 +173,45 @@ __device__ __forceinline__ int64_t upper_bound_rpt(const void *rpt, int is64, in
     return lo;
 }
 
+// Row pointers of the A rows that hold the entries [t0, t1) of a block's
+// tile of A's non-zeros, staged in shared memory so that each thread finds
+// the row of its entries with a short search there instead of a binary
+// search over all of A.rpt in global memory: r[i] = A.rpt[rlo + i] for
+// i < n. n = 0 when they do not fit (long runs of empty rows); the caller
+// then searches global memory. Synchronises the block.
+template <int CAP>
+struct TileRpt {
+    long long r[CAP + 1];
+    long long rlo;
+    int n;
+};
+
+template <int CAP>
+__device__ __forceinline__ void stage_tile_rpt(const Operands &op, int64_t lo, int64_t hi, int64_t t0,
+                                               int64_t t1, TileRpt<CAP> *tr) {
+    __syncthreads();   // readers of the previous tile are done
+    if (threadIdx.x == 0) {
+        const int64_t rlo = upper_bound_rpt(op.arpt, op.a64, lo, hi, t0);
+        const int64_t rhi = upper_bound_rpt(op.arpt, op.a64, rlo, hi, t1 - 1);
+        tr->rlo = rlo;
+        tr->n = rhi - rlo + 2 <= CAP + 1 ? static_cast<int>(rhi - rlo + 2) : 0;
+    }
+    __syncthreads();
+    const int n = tr->n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tr->r[i] = ld_rpt(op.arpt, op.a64, tr->rlo + i);
+    __syncthreads();
+}
+
+// Largest i in [lo, n - 1) with r[i] <= p (r[lo] <= p assumed).
+__device__ __forceinline__ int tile_row(const long long *r, int lo, int n, int64_t p) {
+    int hi = n - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (r[mid] <= p) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 }  // namespace ops
 
 namespace ops {

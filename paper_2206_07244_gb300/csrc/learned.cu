@@ -28,16 +28,27 @@ constexpr int kFeatItems = 8;
 
 __global__ void __launch_bounds__(kFeatBlock)
 feature_scan_kernel(Operands op, long long *nprod, unsigned *maxlen, unsigned *minlen) {
+    constexpr int kTile = kFeatBlock * kFeatItems;
+    __shared__ TileRpt<kTile> tr;
     const int64_t lo = op.row0, hi = op.row0 + op.mw;
     const int64_t pb = ld_rpt(op.arpt, op.a64, lo);
     const int64_t pe = ld_rpt(op.arpt, op.a64, hi);
-    const int64_t tile = static_cast<int64_t>(blockDim.x) * kFeatItems;
-    for (int64_t base = pb + static_cast<int64_t>(blockIdx.x) * tile; base < pe;
-         base += static_cast<int64_t>(gridDim.x) * tile) {
+    for (int64_t base = pb + static_cast<int64_t>(blockIdx.x) * kTile; base < pe;
+         base += static_cast<int64_t>(gridDim.x) * kTile) {
+        stage_tile_rpt<kTile>(op, lo, hi, base, base + kTile < pe ? base + kTile : pe, &tr);
         const int64_t p0 = base + static_cast<int64_t>(threadIdx.x) * kFeatItems;
         if (p0 >= pe) continue;
-        int64_t row = upper_bound_rpt(op.arpt, op.a64, lo, hi, p0);
-        int64_t next = ld_rpt(op.arpt, op.a64, row + 1);
+        const int n = tr.n;
+        int ti = 0;
+        int64_t row, next;
+        if (n > 0) {
+            ti = tile_row(tr.r, 0, n, p0);
+            row = tr.rlo + ti;
+            next = tr.r[ti + 1];
+        } else {
+            row = upper_bound_rpt(op.arpt, op.a64, lo, hi, p0);
+            next = ld_rpt(op.arpt, op.a64, row + 1);
+        }
         long long acc = 0;
         unsigned mx = 0, mn = UINT_MAX;
         auto flush = [&]() {
@@ -55,8 +66,14 @@ feature_scan_kernel(Operands op, long long *nprod, unsigned *maxlen, unsigned *m
                 acc = 0;
                 mx = 0;
                 mn = UINT_MAX;
-                row = upper_bound_rpt(op.arpt, op.a64, row + 1, hi, p);
-                next = ld_rpt(op.arpt, op.a64, row + 1);
+                if (n > 0) {
+                    ti = tile_row(tr.r, ti + 1, n, p);
+                    row = tr.rlo + ti;
+                    next = tr.r[ti + 1];
+                } else {
+                    row = upper_bound_rpt(op.arpt, op.a64, row + 1, hi, p);
+                    next = ld_rpt(op.arpt, op.a64, row + 1);
+                }
             }
             const int k = __ldg(op.acol + p);
             const long long len = ld_rpt(op.brpt, op.b64, k + 1) - ld_rpt(op.brpt, op.b64, k);

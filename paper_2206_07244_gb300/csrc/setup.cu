@@ -28,16 +28,27 @@ __device__ __forceinline__ void flush_row(int64_t *nprod, int64_t row, long long
 
 __global__ void __launch_bounds__(kNprodBlock)
 nprod_kernel(Operands op, int64_t *nprod) {
+    constexpr int kTile = kNprodBlock * kNprodItems;
+    __shared__ TileRpt<kTile> tr;
     const int64_t lo = op.row0, hi = op.row0 + op.mw;     // A rows of the window
     const int64_t pb = ld_rpt(op.arpt, op.a64, lo);
     const int64_t pe = ld_rpt(op.arpt, op.a64, hi);
-    const int64_t tile = static_cast<int64_t>(blockDim.x) * kNprodItems;
-    for (int64_t base = pb + static_cast<int64_t>(blockIdx.x) * tile; base < pe;
-         base += static_cast<int64_t>(gridDim.x) * tile) {
+    for (int64_t base = pb + static_cast<int64_t>(blockIdx.x) * kTile; base < pe;
+         base += static_cast<int64_t>(gridDim.x) * kTile) {
+        stage_tile_rpt<kTile>(op, lo, hi, base, base + kTile < pe ? base + kTile : pe, &tr);
         const int64_t p0 = base + static_cast<int64_t>(threadIdx.x) * kNprodItems;
         if (p0 >= pe) continue;
-        int64_t row = upper_bound_rpt(op.arpt, op.a64, lo, hi, p0);
-        int64_t next = ld_rpt(op.arpt, op.a64, row + 1);
+        const int n = tr.n;
+        int ti = 0;
+        int64_t row, next;
+        if (n > 0) {
+            ti = tile_row(tr.r, 0, n, p0);
+            row = tr.rlo + ti;
+            next = tr.r[ti + 1];
+        } else {
+            row = upper_bound_rpt(op.arpt, op.a64, lo, hi, p0);
+            next = ld_rpt(op.arpt, op.a64, row + 1);
+        }
         long long acc = 0;
 #pragma unroll
         for (int j = 0; j < kNprodItems; ++j) {
@@ -46,8 +57,14 @@ nprod_kernel(Operands op, int64_t *nprod) {
             if (p >= next) {
                 flush_row(nprod, row - lo, acc);
                 acc = 0;
-                row = upper_bound_rpt(op.arpt, op.a64, row + 1, hi, p);
-                next = ld_rpt(op.arpt, op.a64, row + 1);
+                if (n > 0) {
+                    ti = tile_row(tr.r, ti + 1, n, p);
+                    row = tr.rlo + ti;
+                    next = tr.r[ti + 1];
+                } else {
+                    row = upper_bound_rpt(op.arpt, op.a64, row + 1, hi, p);
+                    next = ld_rpt(op.arpt, op.a64, row + 1);
+                }
             }
             const int k = __ldg(op.acol + p);
             acc += ld_rpt(op.brpt, op.b64, k + 1) - ld_rpt(op.brpt, op.b64, k);
