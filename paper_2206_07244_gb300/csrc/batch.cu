@@ -73,12 +73,12 @@ __device__ __forceinline__ bool bsym_insert(int *tab, int key, int &cnt) {
 }
 
 template <int T>
-__device__ __forceinline__ bool bnum_insert(int *tk, double *tv, int key, double v) {
+__device__ __forceinline__ bool bnum_insert(int *tk, double *tv, int key, double a, double b) {
     uint32_t h = hash_slot<T>(key);
     for (int it = 0; it < T; ++it) {
         const int old = atomicCAS(tk + h, -1, key);
         if (old == -1 || old == key) {
-            atomicAdd(tv + h, v);
+            smem_fma_add(tv + h, a, b);
             return true;
         }
         h = next_slot<T>(h);
@@ -99,7 +99,7 @@ __device__ __forceinline__ bool batch_row(const BatchProb &P, int64_t row, int *
         const int64_t q1 = bload_rpt<COHERENT>(P.brpt, P.b64, k + 1);
         for (int64_t q = bload_rpt<COHERENT>(P.brpt, P.b64, k); q < q1; ++q) {
             const int key = bload_col<COHERENT>(P.bcol, q);
-            if (NUMERIC) ok &= bnum_insert<T>(tk, tv, key, a * bload_val<COHERENT>(P.bval, q));
+            if (NUMERIC) ok &= bnum_insert<T>(tk, tv, key, a, bload_val<COHERENT>(P.bval, q));
             else ok &= bsym_insert<T>(tk, key, cnt);
         }
     }
@@ -133,11 +133,12 @@ __device__ __forceinline__ bool tiny_rows(const BatchProb &P, int64_t r0, int64_
             const int64_t q1 = bload_rpt<COHERENT>(P.brpt, P.b64, k + 1);
             for (int64_t q = bload_rpt<COHERENT>(P.brpt, P.b64, k); q < q1; ++q) {
                 const int key = bload_col<COHERENT>(P.bcol, q);
-                const double v = NUMERIC ? a * bload_val<COHERENT>(P.bval, q) : 0.0;
+                const double b = NUMERIC ? bload_val<COHERENT>(P.bval, q) : 0.0;
                 int pos = 0;
                 while (pos < n && keys[pos * kBatchBlock + t] < key) ++pos;
                 if (pos < n && keys[pos * kBatchBlock + t] == key) {
-                    if (NUMERIC) vals[pos * kBatchBlock + t] += v;
+                    // one fused multiply-add per product (float64 is scarce here)
+                    if (NUMERIC) vals[pos * kBatchBlock + t] = fma(a, b, vals[pos * kBatchBlock + t]);
                     continue;
                 }
                 if (n == kBatchTiny) {   // a ninth distinct column: the row goes to the tables
@@ -149,7 +150,7 @@ __device__ __forceinline__ bool tiny_rows(const BatchProb &P, int64_t r0, int64_
                     if (NUMERIC) vals[m * kBatchBlock + t] = vals[(m - 1) * kBatchBlock + t];
                 }
                 keys[pos * kBatchBlock + t] = key;
-                if (NUMERIC) vals[pos * kBatchBlock + t] = v;
+                if (NUMERIC) vals[pos * kBatchBlock + t] = fma(a, b, 0.0);   // 0 + a b, as the sum starts
                 ++n;
             }
         }

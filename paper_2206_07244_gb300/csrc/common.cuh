@@ -173,6 +173,25 @@ __device__ __forceinline__ int64_t upper_bound_rpt(const void *rpt, int is64, in
     return lo;
 }
 
+// *p = fma(a, b, *p) as one atomic update of a shared-memory float64: a
+// compare-and-swap loop on the value's bits. One fused multiply-add per
+// product instead of a multiply and an atomic add (whose add also runs on
+// the float64 pipe, which this GPU has little of); fma rounds once, so the
+// sum is at least as accurate. Some update succeeds in every round of
+// competing threads, so the loop ends.
+__device__ __forceinline__ void smem_fma_add(double *p, double a, double b) {
+    unsigned long long *q = reinterpret_cast<unsigned long long *>(p);
+    unsigned long long old = *reinterpret_cast<volatile unsigned long long *>(q);
+    for (;;) {
+        const unsigned long long want =
+            static_cast<unsigned long long>(__double_as_longlong(fma(a, b, __longlong_as_double(
+                static_cast<long long>(old)))));
+        const unsigned long long got = atomicCAS(q, old, want);
+        if (got == old) return;
+        old = got;
+    }
+}
+
 // Row pointers of the A rows that hold the entries [t0, t1) of a block's
 // tile of A's non-zeros, staged in shared memory so that each thread finds
 // the row of its entries with a short search there instead of a binary

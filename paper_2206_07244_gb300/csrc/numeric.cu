@@ -29,12 +29,12 @@ namespace ops {
 
 // Returns false when every slot holds another key (the table is full).
 template <int T>
-__device__ __forceinline__ bool num_insert(int *tk, double *tv, int key, double v) {
+__device__ __forceinline__ bool num_insert(int *tk, double *tv, int key, double a, double b) {
     uint32_t h = hash_slot<T>(key);
     for (int it = 0; it < T; ++it) {
         const int old = atomicCAS(tk + h, -1, key);
         if (old == -1 || old == key) {
-            atomicAdd(tv + h, v);
+            smem_fma_add(tv + h, a, b);
             return true;
         }
         h = next_slot<T>(h);
@@ -171,11 +171,11 @@ num_hash_kernel(Operands op, BinWork w) {
         WalkScratch *sc = reinterpret_cast<WalkScratch *>(
             smem_raw + (sizeof(int) + sizeof(double)) * (size_t)RPB * T);
         block_row_walk<BLOCK, true>(op, p0, p1, S, sc, [&](int key, double a, double b) {
-            if (!num_insert<T>(tk, tv, key, a * b)) failed = true;
+            if (!num_insert<T>(tk, tv, key, a, b)) failed = true;
         });
     } else {
         group_row_walk<TPR, true>(op, p0, p1, S, [&](int key, double a, double b) {
-            if (!num_insert<T>(tk, tv, key, a * b)) failed = true;
+            if (!num_insert<T>(tk, tv, key, a, b)) failed = true;
         });
     }
     if (failed) {
