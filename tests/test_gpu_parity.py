@@ -137,6 +137,38 @@ def test_each_numeric_kernel(kernel):
     assert bins[0] > 0
 
 
+def contended_product(seed):
+    """Rows whose products pile onto a few columns: each A row has 100 to 250
+    entries and every B row holds 6 to 10 of the same 12 columns, so many
+    lanes update one table slot at once. Small integer values keep every
+    sum exact in float64."""
+    rng = np.random.default_rng(seed)
+    m, k, n = 192, 300, 40
+    a_rows = [np.sort(rng.choice(k, rng.integers(100, 251), replace=False)) for _ in range(m)]
+    hot = rng.choice(n, 12, replace=False)
+    b_rows = [np.sort(rng.choice(hot, rng.integers(6, 11), replace=False)) for _ in range(k)]
+
+    def csr(rows, ncols):
+        rpt = np.zeros(len(rows) + 1, dtype=np.int32)
+        rpt[1:] = np.cumsum([len(r) for r in rows])
+        col = np.concatenate(rows).astype(np.int32)
+        val = rng.integers(-3, 4, col.size).astype(np.float64)
+        return W.Csr(len(rows), ncols, rpt, col, val)
+    return csr(a_rows, k), csr(b_rows, n)
+
+
+@pytest.mark.parametrize("kernel", range(len(ops.kernel_table(1)) if torch.cuda.is_available() else 0))
+def test_contended_slot_updates_each_numeric_kernel(kernel):
+    # every numeric kernel, many concurrent updates of one slot: the
+    # compare-and-swap update must lose none of them (bit-exact sums)
+    A, B = contended_product(60 + kernel)
+    with ops.Handle(forced(1, kernel)) as h:
+        got = gpu_product(A, B, h)
+        bins = h.stats()["num_bins"]
+    check(A, B, got, exact=True)
+    assert bins[0] == A.rows
+
+
 @pytest.mark.parametrize("lanes", [1, 4, 32])
 def test_fixed_lanes_per_b_row(lanes):
     A = W.rmat(10, 16, seed=8)
