@@ -48,6 +48,8 @@ WORKLOADS = {
                lambda: W.rmat(18, 16, seed=1)),
     "rmat16": ("C = A*A, A = R-MAT n=2^16, degree 16, seed 1 (small profiling case)",
                lambda: W.rmat(16, 16, seed=1)),
+    "blockdiag20": ("C = A*A, A = random block-diagonal n=2^20, 1024 blocks, mean degree 24, seed 7",
+                    lambda: W.block_diagonal(1 << 20, 1024, 24.0, seed=7)),
 }
 
 SLOT_NAMES = ([f"sym_bin{j}" for j in range(16)] + [f"num_bin{j}" for j in range(16)]

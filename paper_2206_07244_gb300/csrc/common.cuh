@@ -1,6 +1,7 @@
 // Device helpers shared by the SpGEMM kernels (sm_103a).
 #pragma once
 
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -128,6 +129,19 @@ __device__ __forceinline__ V group_sum(V v, V *red) {
         V t = (l < (TPR >> 5)) ? red[l] : V(0);
         return warp_sum_xor(t, 32);  // every warp forms the same total
     }
+}
+
+// Minimum over a block of BLOCK threads (BLOCK a multiple of 32); every
+// thread gets it. `red` holds 32 ints.
+template <int BLOCK>
+__device__ __forceinline__ int block_min(int v, int *red) {
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();   // earlier readers of `red` are done
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int t = (threadIdx.x & 31) < (BLOCK >> 5) ? red[threadIdx.x & 31] : INT_MAX;
+    for (int o = 16; o > 0; o >>= 1) t = min(t, __shfl_xor_sync(0xffffffffu, t, o));
+    return t;
 }
 
 // Exclusive count of `flag` over the row group in thread order, plus the

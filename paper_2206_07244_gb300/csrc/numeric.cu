@@ -186,6 +186,7 @@ num_hash_kernel(Operands op, BinWork w) {
     // condense: occupied slots move to the front, chunk by chunk; a write
     // never lands past the chunk that was just read.
     int n = 0;
+    int kmin = INT_MAX, kmax = -1;   // this thread's smallest and largest key
     for (int c = 0; c < T; c += TPR) {
         const int s = c + lg;
         int k = -1;
@@ -193,6 +194,10 @@ num_hash_kernel(Operands op, BinWork w) {
         if (s < T) {
             k = tk[s];
             v = tv[s];
+        }
+        if (k >= 0) {
+            kmin = min(kmin, k);
+            kmax = max(kmax, k);
         }
         int pre, tot;
         group_excl_count<TPR>(k >= 0, pre, tot, red32);
@@ -254,6 +259,67 @@ num_hash_kernel(Operands op, BinWork w) {
             else if (n <= 128 || T <= 128) warp_sort_store<(T < 128 ? T / 32 : 4)>(tk, tv, n, m, ocol, oval, store);
             else warp_sort_store<T / 32>(tk, tv, n, m, ocol, oval, store);
             return;   // uniform over the warp; no block barrier follows
+        }
+    }
+    if constexpr (TPR > 32) {
+        // One row per block. When the row's columns span at most 8T, each
+        // entry goes straight to its place in the sorted row: bit
+        // (column - min) of a span bitmap is set for every entry, and the
+        // set bits below it give its rank. The bitmap and its per-word
+        // prefix counts (T/4 words each at most) use the table's free upper
+        // half; every entry is in the lower half (n <= T/2).
+        if (n > 0 && n <= T / 2) {   // uniform: n is the block's count
+            kmin = block_min<TPR>(kmin, red32);
+            kmax = -block_min<TPR>(-kmax, red32);
+            const long long span = static_cast<long long>(kmax) - kmin + 1;
+            if (span <= 8ll * T) {   // uniform
+                const int nw = static_cast<int>((span + 31) >> 5);
+                unsigned *bits = reinterpret_cast<unsigned *>(tk + T / 2);
+                unsigned *pre = bits + T / 4;
+                for (int i = lg; i < nw; i += TPR) bits[i] = 0u;
+                __syncthreads();
+                for (int s = lg; s < n; s += TPR) {
+                    const unsigned rel = static_cast<unsigned>(tk[s] - kmin);
+                    atomicOr(bits + (rel >> 5), 1u << (rel & 31));
+                }
+                __syncthreads();
+                // rank of each word's first column: thread lg owns words
+                // [lg * per, (lg + 1) * per)
+                const int per = (nw + TPR - 1) / TPR;
+                const int w0 = lg * per, w1 = min(w0 + per, nw);
+                unsigned mine = 0;
+                for (int i = w0; i < w1; ++i) mine += __popc(bits[i]);
+                unsigned total;
+                unsigned run = block_excl_scan<TPR>(mine, total, reinterpret_cast<unsigned *>(red32));
+                for (int i = w0; i < w1; ++i) {
+                    pre[i] = run;
+                    run += __popc(bits[i]);
+                }
+                __syncthreads();
+                if (valid) {
+                    const int64_t m = n < n_expect ? n : n_expect;
+                    int32_t *ocol = w.ccol + cbase;
+                    double *oval = w.cval + cbase;
+                    bool in_bounds = true;
+                    if (ONE_PHASE) {
+                        ocol = w.tcol + w.tbase + r * w.tcap;
+                        oval = w.tval + w.tbase + r * w.tcap;
+                        in_bounds = m <= w.tcap && w.tbase + r * w.tcap + m <= w.tlimit;
+                        if (!in_bounds && lg == 0) set_error(w.err, DERR_BOUNDS);
+                    }
+                    for (int s = lg; in_bounds && s < n; s += TPR) {
+                        const int key = tk[s];
+                        const unsigned rel = static_cast<unsigned>(key - kmin);
+                        const unsigned wd = rel >> 5;
+                        const int64_t rank = pre[wd] + __popc(bits[wd] & ((1u << (rel & 31)) - 1u));
+                        if (rank < m) {
+                            ocol[rank] = key;
+                            oval[rank] = tv[s];
+                        }
+                    }
+                }
+                return;   // uniform over the block
+            }
         }
     }
     for (int s = n + lg; s < P; s += TPR) tk[s] = INT_MAX;
