@@ -262,20 +262,21 @@ num_hash_kernel(Operands op, BinWork w) {
         }
     }
     if constexpr (TPR > 32) {
-        // One row per block. When the row's columns span at most 8T, each
-        // entry goes straight to its place in the sorted row: bit
+        // One row per block. When the row's columns span few enough words,
+        // each entry goes straight to its place in the sorted row: bit
         // (column - min) of a span bitmap is set for every entry, and the
-        // set bits below it give its rank. The bitmap and its per-word
-        // prefix counts (T/4 words each at most) use the table's free upper
-        // half; every entry is in the lower half (n <= T/2).
-        if (n > 0 && n <= T / 2) {   // uniform: n is the block's count
+        // set bits below it give its rank. The bitmap (nw words) and its
+        // per-word prefix counts (nw words) take the top 2 nw words of the
+        // key table, above the n condensed keys.
+        if (n > 0) {   // uniform: n is the block's count
             kmin = block_min<TPR>(kmin, red32);
             kmax = -block_min<TPR>(-kmax, red32);
             const long long span = static_cast<long long>(kmax) - kmin + 1;
-            if (span <= 8ll * T) {   // uniform
-                const int nw = static_cast<int>((span + 31) >> 5);
-                unsigned *bits = reinterpret_cast<unsigned *>(tk + T / 2);
-                unsigned *pre = bits + T / 4;
+            const long long nwl = (span + 31) >> 5;
+            if (n + 2 * nwl <= T) {   // uniform
+                const int nw = static_cast<int>(nwl);
+                unsigned *bits = reinterpret_cast<unsigned *>(tk + T - 2 * nw);
+                unsigned *pre = bits + nw;
                 for (int i = lg; i < nw; i += TPR) bits[i] = 0u;
                 __syncthreads();
                 for (int s = lg; s < n; s += TPR) {

@@ -169,6 +169,64 @@ def test_contended_slot_updates_each_numeric_kernel(kernel):
     assert bins[0] == A.rows
 
 
+def narrow_rows(seed, m=160, width=700, per_row=(130, 240)):
+    """A with rows of 130 to 240 entries inside a window of `width`
+    columns that slides along the diagonal, integer values: C = A * I has
+    the same narrow rows."""
+    rng = np.random.default_rng(seed)
+    n = m + width
+    rows = []
+    for i in range(m):
+        k = rng.integers(per_row[0], per_row[1] + 1)
+        rows.append(np.sort(rng.choice(width, k, replace=False) + i))
+    rpt = np.zeros(m + 1, dtype=np.int32)
+    rpt[1:] = np.cumsum([len(r) for r in rows])
+    col = np.concatenate(rows).astype(np.int32)
+    A = W.Csr(m, n, rpt, col, rng.integers(-5, 6, col.size).astype(np.float64))
+    I = W.Csr(n, n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.ones(n))
+    return A, I
+
+
+@pytest.mark.parametrize("kernel", range(len(ops.kernel_table(1)) if torch.cuda.is_available() else 0))
+def test_narrow_rows_each_numeric_kernel(kernel):
+    # rows whose columns span a few hundred: block-per-row kernels place
+    # them by rank in a span bitmap, the others sort; C = A * I = A exactly
+    A, I = narrow_rows(70 + kernel)
+    cap = ops.kernel_table(1)[kernel][3]
+    if cap != -1 and cap < 240:
+        pytest.skip("rows larger than this kernel's tables")
+    with ops.Handle(forced(1, kernel)) as h:
+        got = gpu_product(A, I, h)
+        bins = h.stats()["num_bins"]
+    check(A, I, got, exact=True)
+    assert bins[0] == A.rows
+
+
+@pytest.mark.parametrize("extra", [0, 1])
+def test_span_bitmap_boundary(extra):
+    # the 512-slot kernel (64 threads) places a row of n entries by bitmap
+    # rank when its span bitmap and prefix counts (2 words per 32 columns)
+    # fit above the keys, n + 2 ceil(span / 32) <= 512, and sorts it
+    # otherwise: rows of 182 entries spanning 5280 and 5281 columns
+    table = ops.kernel_table(1)
+    kernel = next(k for k, t in enumerate(table) if t[0] == 64 and t[2] == 512)
+    rng = np.random.default_rng(80 + extra)
+    last = 5279 + extra
+    n = last + 65
+    rows = []
+    for i in range(24):
+        mid = rng.choice(np.arange(1, last), 180, replace=False)
+        rows.append(np.sort(np.concatenate([[0], mid, [last]])))
+    rpt = np.zeros(len(rows) + 1, dtype=np.int32)
+    rpt[1:] = np.cumsum([len(r) for r in rows])
+    col = np.concatenate(rows).astype(np.int32)
+    A = W.Csr(len(rows), n, rpt, col, rng.integers(-5, 6, col.size).astype(np.float64))
+    I = W.Csr(n, n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.ones(n))
+    with ops.Handle(forced(1, kernel)) as h:
+        got = gpu_product(A, I, h)
+    check(A, I, got, exact=True)
+
+
 @pytest.mark.parametrize("lanes", [1, 4, 32])
 def test_fixed_lanes_per_b_row(lanes):
     A = W.rmat(10, 16, seed=8)
