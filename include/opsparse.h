@@ -158,6 +158,31 @@ int spgemm_numeric(spgemm_handle *h, const spgemm_csr_in *A,
 int spgemm_multiply(spgemm_handle *h, const spgemm_csr_in *A,
                     const spgemm_csr_in *B, spgemm_csr_out *C);
 
+/* Numeric phase again over the structure of this handle's last
+ * spgemm_numeric, for new values of A and B with the same structure (the
+ * same rpt and col contents): the repeated products of an iterative setup
+ * where only the values change. It rests on the two-phase split of Sec. 2.2
+ * (structure first, values second); the paper itself always runs both.
+ * Skips n_prod, both binning steps, the symbolic kernels, the scan and the
+ * allocation: the rows keep the bins, kernels and C.rpt of the last call,
+ * and only the per-bin numeric kernels run (Algorithm 5; large rows the
+ * bitmap-rank kernel, with its whole-row pass 2).
+ *   A, B  device CSR, caller-owned; rows, cols and nnz must equal those of
+ *         the last numeric call and A.val/B.val must be non-NULL.
+ *   C     the output of that call (or arrays with the same contents):
+ *         C->rpt (int64, rows+1) is read, C->col is rewritten with the same
+ *         columns and C->val (nnz float64) receives the new values. Nothing
+ *         is allocated and ownership does not change.
+ * Returns SPGEMM_ERR_STATE when the handle holds no plain-mode structure
+ * (no numeric call yet, a spgemm_symbolic, spgemm_multiply_host or
+ * spgemm_set_config since, or the last call was in SPGEMM_MODE_LEARNED) or
+ * the shapes differ; SPGEMM_ERR_INVALID for a C that does not describe that
+ * result. A or B with another structure but the same sizes is not detected
+ * here: spgemm_status then reports SPGEMM_ERR_INTERNAL where a row's size no
+ * longer matches, and C is undefined. Does not synchronise. */
+int spgemm_numeric_values(spgemm_handle *h, const spgemm_csr_in *A,
+                          const spgemm_csr_in *B, const spgemm_csr_out *C);
+
 /* Wait for the handle's stream and report device-side checks raised by any
  * earlier call (a full hash table, a row whose numeric size differs from its
  * symbolic count): SPGEMM_OK or SPGEMM_ERR_INTERNAL (the check is then

@@ -181,6 +181,24 @@ class Handle:
         self.symbolic(A, B)
         return self.numeric(A, B)
 
+    def numeric_values(self, A: CSR, B: CSR, C: CSR) -> CSR:
+        """New values of C for A and B with the structure of the last
+        ``numeric`` call (same rpt and col, new val): only the numeric kernels
+        run, over the rows' kept bins. ``C`` is that call's result; its val
+        (and, with the same columns, its col) is overwritten in place."""
+        import torch
+        a, b = _csr_in(A), _csr_in(B)
+        if C.rpt.dtype != torch.int64 or not (C.rpt.is_cuda and C.col.is_cuda and C.val.is_cuda):
+            raise ValueError("C must be a CUDA CSR with an int64 row pointer")
+        c = _abi.CsrOut()
+        c.rows, c.cols, c.nnz = C.rows, C.cols, C.nnz
+        c.rpt = C.rpt.data_ptr()
+        c.col = C.col.data_ptr() if C.nnz else None
+        c.val = C.val.data_ptr() if C.nnz else None
+        _abi.check(self._lib.spgemm_numeric_values(self._h, ctypes.byref(a), ctypes.byref(b),
+                                                   ctypes.byref(c)), "spgemm_numeric_values")
+        return C
+
     def _wrap(self, c: _abi.CsrOut, out) -> CSR:
         import torch
         rows, nnz = int(c.rows), int(c.nnz)

@@ -18,7 +18,7 @@ ERRORS = {0: "SPGEMM_OK", -1: "SPGEMM_ERR_INVALID", -2: "SPGEMM_ERR_SHAPE",
 # exports them all).
 EXPORTS = [
     "spgemm_create", "spgemm_set_config", "spgemm_get_config", "spgemm_symbolic",
-    "spgemm_numeric", "spgemm_multiply", "spgemm_status", "spgemm_free",
+    "spgemm_numeric", "spgemm_numeric_values", "spgemm_multiply", "spgemm_status", "spgemm_free",
     "spgemm_destroy", "spgemm_last_stats", "spgemm_kernel_info", "spgemm_strerror",
     "spgemm_last_cuda_error",
     "spgemm_multiply_host", "spgemm_bin_stats", "spgemm_set_timing", "spgemm_kernel_times",
@@ -91,6 +91,7 @@ def lib(path: str | None = None):
             "spgemm_get_config": [P, P],
             "spgemm_symbolic": [P, P, P, I64, I64, ctypes.POINTER(I64)],
             "spgemm_numeric": [P, P, P, P],
+            "spgemm_numeric_values": [P, P, P, P],
             "spgemm_multiply": [P, P, P, P],
             "spgemm_status": [P],
             "spgemm_free": [P, P],

@@ -89,6 +89,10 @@ struct spgemm_handle {
     long long num_size[kMaxBins] = {};
     RunPlan rplan;               // windowed pass 2 plan of the last symbolic call
     bool b_unsorted = false;     // some row of B has decreasing columns
+    // the last plain numeric call's rows stay in their bins (numeric order)
+    // until the next symbolic call: spgemm_numeric_values runs them again
+    bool reuse = false;
+    int64_t reuse_arows = 0, reuse_annz = 0, reuse_brows = 0, reuse_bnnz = 0;
     int64_t stats[4 + 2 * SPGEMM_MAX_BINS] = {};
     int64_t bin_stats[2][3 * SPGEMM_MAX_BINS] = {};
     // learned sizing
@@ -776,6 +780,7 @@ int spgemm_create(spgemm_handle **out, const spgemm_config *cfg, spgemm_alloc_fn
 
 int spgemm_set_config(spgemm_handle *h, const spgemm_config *cfg) {
     if (!h) return SPGEMM_ERR_INVALID;
+    h->reuse = false;   // the kept rows were binned for the old kernels
     if (!cfg) {
         default_config(h->cfg);
         h->cfg_auto = true;
@@ -801,6 +806,7 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     if ((rc = check_csr_in(B))) return rc;
     if (A->cols != B->rows) return SPGEMM_ERR_SHAPE;
     if (row_begin < 0 || row_end < row_begin || row_end > A->rows) return SPGEMM_ERR_INVALID;
+    h->reuse = false;   // the binning below overwrites the kept rows
     if (h->state == 1) {  // an earlier symbolic result was never consumed
         dev_free(h, h->crpt);
         dev_free(h, h->tcol);
@@ -917,6 +923,7 @@ int spgemm_numeric(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in
     const bool given = C->col != nullptr && C->val != nullptr;
     // from here on the symbolic result is consumed
     h->state = 0;
+    h->reuse = false;
     int64_t *crpt = h->crpt;
     h->crpt = nullptr;
     const Operands op = make_operands(A, B, h->row0, h->mw);
@@ -997,6 +1004,11 @@ int spgemm_numeric(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in
     rc = run_bins(h, 1, op, h->num_size, off, nid, crpt, ccol, cval, &rp);
     dev_free(h, bs);
     if (rc) return fail(rc);
+    h->reuse = true;
+    h->reuse_arows = A->rows;
+    h->reuse_annz = A->nnz;
+    h->reuse_brows = B->rows;
+    h->reuse_bnnz = B->nnz;
     C->rows = h->mw;
     C->cols = h->ncols;
     C->nnz = h->nnz;
@@ -1004,6 +1016,38 @@ int spgemm_numeric(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in
     C->col = ccol;
     C->val = cval;
     return SPGEMM_OK;
+}
+
+// Numeric kernels again over the kept bins and C.rpt (same structure, new
+// values): no n_prod, binning, symbolic, scan or allocation. The bitmap bin
+// takes the whole-row pass 2 (its windowed form needs a scratch buffer).
+int spgemm_numeric_values(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in *B,
+                          const spgemm_csr_out *C) {
+    if (!h || !C) return SPGEMM_ERR_INVALID;
+    int rc = check_csr_in(A);
+    if (rc) return rc;
+    if ((rc = check_csr_in(B))) return rc;
+    if (A->cols != B->rows) return SPGEMM_ERR_SHAPE;
+    if (!h->reuse) return SPGEMM_ERR_STATE;
+    if (A->rows != h->reuse_arows || A->nnz != h->reuse_annz || B->rows != h->reuse_brows ||
+        B->nnz != h->reuse_bnnz || B->cols != h->ncols)
+        return SPGEMM_ERR_STATE;
+    if ((A->nnz > 0 && !A->val) || (B->nnz > 0 && !B->val)) return SPGEMM_ERR_INVALID;
+    if (C->rows != h->mw || C->cols != h->ncols || C->nnz != h->nnz || !C->rpt ||
+        (C->nnz > 0 && (!C->col || !C->val)))
+        return SPGEMM_ERR_INVALID;
+    const int nb = h->cfg.num_nbins;
+    long long off[kMaxBins] = {};
+    long long acc = 0;
+    int nonempty = 0;
+    for (int j = 0; j < nb; ++j) {
+        off[j] = acc;
+        acc += h->num_size[j];
+        nonempty += h->num_size[j] > 0;
+    }
+    const Operands op = make_operands(A, B, h->row0, h->mw);
+    return run_bins(h, 1, op, h->num_size, off, nonempty <= 1, static_cast<int64_t *>(C->rpt), C->col,
+                    C->val, nullptr);
 }
 
 int spgemm_multiply(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in *B,
@@ -1041,7 +1085,7 @@ int spgemm_last_stats(const spgemm_handle *h, int64_t *out, int n) {
     return SPGEMM_OK;
 }
 
-int spgemm_multiply_host(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in *B,
+static int multiply_host(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in *B,
                          int64_t chunk_bytes, spgemm_host_sink_fn sink, void *ctx,
                          int64_t *nnzC) {
     if (!h || !A || !B || !sink) return SPGEMM_ERR_INVALID;
@@ -1274,6 +1318,14 @@ int spgemm_multiply_host(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_
     destroy_events();
     release();
     if (rc == SPGEMM_OK && nnzC) *nnzC = nnz_total;
+    return rc;
+}
+
+int spgemm_multiply_host(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in *B,
+                         int64_t chunk_bytes, spgemm_host_sink_fn sink, void *ctx,
+                         int64_t *nnzC) {
+    const int rc = multiply_host(h, A, B, chunk_bytes, sink, ctx, nnzC);
+    if (h) h->reuse = false;   // its device copies of A, B and C are gone
     return rc;
 }
 
