@@ -353,7 +353,12 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned &total,
 // call it (it synchronises the block). A lane's products of one piece (at
 // most kPieceIters) are loaded together before any of them is used, so each
 // thread keeps several L2 loads in flight.
-template <int BLOCK, bool NEED_VAL, int ITERS = kPieceIters, typename F>
+// KEEP: a first walk of a row also stores the A values of its entries, and a
+// later walk of the same row with the same S and ITERS and the scratch left
+// untouched in between (KEEP = 2) reuses the entries' B-row offsets, lengths,
+// A values and piece offsets when the row fits one chunk, instead of loading
+// them and scanning again.
+template <int BLOCK, bool NEED_VAL, int ITERS = kPieceIters, int KEEP = 0, typename F>
 __device__ __forceinline__ void block_row_walk(const Operands &op, int64_t p0, int64_t p1, int S,
                                                WalkScratch *sc, F &&f) {
     static_assert(BLOCK >= 32 && BLOCK % 32 == 0, "block walk needs whole warps");
@@ -362,24 +367,28 @@ __device__ __forceinline__ void block_row_walk(const Operands &op, int64_t p0, i
     const long long W = static_cast<long long>(S) * ITERS;
     for (int64_t c = p0; c < p1; c += CH) {
         const int cnt = static_cast<int>(p1 - c < CH ? p1 - c : CH);
-        long long pieces = 0;
-        if (threadIdx.x < CH) {
-            const int t = threadIdx.x;
-            if (t < cnt) {
-                const int k = __ldg(op.acol + c + t);
-                const long long q0 = ld_rpt(op.brpt, op.b64, k);
-                const long long len = ld_rpt(op.brpt, op.b64, k + 1) - q0;
-                sc->q0[t] = q0;
-                sc->len[t] = static_cast<int>(len);
-                if (NEED_VAL) sc->a[t] = __ldg(op.aval + c + t);
-                pieces = (len + W - 1) / W;
-            }
-        }
         long long total;
-        const long long ex = block_excl_scan_ll<BLOCK>(pieces, total, sc->warp_tot);
-        if (threadIdx.x < CH) sc->pstart[threadIdx.x] = ex;   // entries >= cnt hold `total`
-        if (threadIdx.x == 0) sc->pstart[CH] = total;
-        __syncthreads();
+        if (KEEP == 2 && p1 - p0 <= CH) {
+            total = sc->pstart[CH];
+        } else {
+            long long pieces = 0;
+            if (threadIdx.x < CH) {
+                const int t = threadIdx.x;
+                if (t < cnt) {
+                    const int k = __ldg(op.acol + c + t);
+                    const long long q0 = ld_rpt(op.brpt, op.b64, k);
+                    const long long len = ld_rpt(op.brpt, op.b64, k + 1) - q0;
+                    sc->q0[t] = q0;
+                    sc->len[t] = static_cast<int>(len);
+                    if (NEED_VAL || KEEP == 1) sc->a[t] = __ldg(op.aval + c + t);
+                    pieces = (len + W - 1) / W;
+                }
+            }
+            const long long ex = block_excl_scan_ll<BLOCK>(pieces, total, sc->warp_tot);
+            if (threadIdx.x < CH) sc->pstart[threadIdx.x] = ex;   // entries >= cnt hold `total`
+            if (threadIdx.x == 0) sc->pstart[CH] = total;
+            __syncthreads();
+        }
         // sub-group `sub` takes a contiguous range of pieces: one binary
         // search finds its first entry, later entries follow by stepping
         const long long per = (total + nsub - 1) / nsub;

@@ -489,7 +489,6 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
     unsigned long long *bm = reinterpret_cast<unsigned long long *>(smem_raw + w.head);
     unsigned *bm32 = reinterpret_cast<unsigned *>(bm);   // same words, 32-bit halves
     unsigned *pre = reinterpret_cast<unsigned *>(bm + words);
-    __shared__ long long red64[32];
     __shared__ unsigned sw[33];
     const int64_t row = w.bins ? static_cast<int64_t>(w.bins[w.off + blockIdx.x])
                                : w.off + static_cast<int64_t>(blockIdx.x);
@@ -498,7 +497,10 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
     const int64_t ar = op.row0 + row;
     const int64_t p0 = ld_rpt(op.arpt, op.a64, ar);
     const int64_t p1 = ld_rpt(op.arpt, op.a64, ar + 1);
-    const int S = numeric_lanes<kBmBlock>(op, w.lanes, p0, p1, threadIdx.x, red64);
+    // threads per B row from the row's size instead of its n_prod (C.rpt
+    // holds offsets by now): n_nz <= n_prod, so the choice is at most one
+    // step narrower, and the A row is first read by pass 1 itself
+    const int S = pick_lanes_distinct(w.lanes, n_expect, p1 - p0, 32);
     const int64_t span = static_cast<int64_t>(words) * 64;
     int64_t done = 0;
     bool ok = true;
@@ -511,7 +513,7 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
         // times slower on this GPU
         const int c0i = static_cast<int>(c0);
         const unsigned span32 = static_cast<unsigned>(span);
-        block_row_walk<kBmBlock, false, ITERS>(op, p0, p1, S, sc, [&](int key, double, double) {
+        block_row_walk<kBmBlock, false, ITERS, 1>(op, p0, p1, S, sc, [&](int key, double, double) {
             const unsigned rel = static_cast<unsigned>(key - c0i);   // one compare covers both ends
             if (rel < span32) atomicOr(bm32 + (rel >> 5), 1u << (rel & 31));
         });
@@ -657,8 +659,9 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
             }
             for (int64_t t = threadIdx.x; t < cnt; t += kBmBlock) st_keep(cval + t, 0.0, pol);
             __syncthreads();
-            // pass 2: each product lands on its column's rank
-            block_row_walk<kBmBlock, true, ITERS>(op, p0, p1, S, sc, [&](int key, double a, double b) {
+            // pass 2: each product lands on its column's rank (the walk
+            // scratch of pass 1 is still in place)
+            block_row_walk<kBmBlock, true, ITERS, 2>(op, p0, p1, S, sc, [&](int key, double a, double b) {
                 const unsigned rel = static_cast<unsigned>(key - c0i);
                 if (rel < span32) {
                     const unsigned wi = rel >> 6, bi = rel & 63u;
