@@ -63,7 +63,7 @@ NSLOTS = len(SLOT_NAMES)
 # of a workload's dominant kernel, from an ncu capture of this code (summary
 # and command in profiles/); None where no capture of the current kernel
 # exists.
-TRAFFIC = {("rmat20", "num_bitmap_kernel"): 248_240_038_400 + 222_882_936_832}
+TRAFFIC = {("rmat20", "num_bitmap_kernel"): 235_366_154_496 + 212_000_421_888}
 
 
 def peaks():
