@@ -349,6 +349,57 @@ def batched_eval(count=512, seed=0, reps=3, tune=True):
     return out
 
 
+def hash_ablation_eval(reps=3):
+    """The paper's hashing comparison (Sec. 6): one atomicCAS per probe
+    (Algorithms 4-5, hash_access = 0) against a read of the slot before the
+    compare-and-swap (hash_access = 1), everything else the same, on the
+    27-point stencil 128^3, whose rows all take hash kernels. Kernel times of
+    the symbolic and numeric hash bins, serialised on one stream."""
+    import ctypes
+    import torch
+    import paper_2206_07244_gb300 as ops
+    from paper_2206_07244_gb300 import _abi
+    lib = _abi.lib()
+    S = W.stencil27(128, seed=3)
+    dS = ops.CSR.from_workload(S)
+    del S
+    res = {}
+    for mode in (0, 1):
+        h = ops.Handle()
+        C = h.multiply(dS, dS)        # the default bins for this B
+        del C
+        cfg = h.get_config()
+        cfg["hash_access"] = mode
+        h.set_config(cfg)
+        for _ in range(2):
+            C = h.multiply(dS, dS)
+            del C
+        ms = (ctypes.c_double * NSLOTS)()
+        ln = (ctypes.c_int64 * NSLOTS)()
+        _abi.check(lib.spgemm_set_timing(h._h, 2), "spgemm_set_timing")
+        _abi.check(lib.spgemm_kernel_times(h._h, ms, ln, NSLOTS, 1), "spgemm_kernel_times")
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            C = h.multiply(dS, dS)
+            del C
+        e1.record(s)
+        h.status()
+        _abi.check(lib.spgemm_kernel_times(h._h, ms, ln, NSLOTS, 1), "spgemm_kernel_times")
+        lib.spgemm_set_timing(h._h, 0)
+        nbs, nbn = len(ops.kernel_table(0)) - 1, len(ops.kernel_table(1)) - 1
+        sym = sum(ms[j] for j, k in enumerate(cfg["sym_kernel"]) if k != nbs) / reps
+        num = sum(ms[16 + j] for j, k in enumerate(cfg["num_kernel"]) if k != nbn) / reps
+        res[mode] = {"sym_hash_ms": round(sym, 3), "num_hash_ms": round(num, 3),
+                     "multiply_ms_serial": round(e0.elapsed_time(e1) / reps, 3)}
+        h.close()
+    return {"workload": "C = A*A, A = 27-point stencil 128^3 (every row in a hash bin)",
+            "single_access": res[0], "multi_access": res[1],
+            "sym_speedup_single_over_multi": round(res[1]["sym_hash_ms"] / max(res[0]["sym_hash_ms"], 1e-9), 3),
+            "num_speedup_single_over_multi": round(res[1]["num_hash_ms"] / max(res[0]["num_hash_ms"], 1e-9), 3)}
+
+
 def pick_slab(A, budget_entries):
     """A contiguous row slab of A*A, starting at row A.rows/2, whose C has at
     most budget_entries entries (sized with the library's symbolic phase)."""
@@ -415,12 +466,14 @@ def main():
     ap.add_argument("--window-lists", type=int, default=None,
                     help="set the numeric bitmap kernel's window_lists option on top of the "
                          "configuration in use (0 = whole-row pass 2)")
-    ap.add_argument("--legs", default="all", choices=["all", "none", "learned", "batched"],
+    ap.add_argument("--legs", default="all", choices=["all", "none", "learned", "batched", "ablation"],
                     help="extra comparisons after the main line: learned sizing vs plain "
-                         "(trained weights) and 512 Galerkin products plain vs batched")
+                         "(trained weights), 512 Galerkin products plain vs batched, and "
+                         "single- vs multi-access hash probes")
     args = ap.parse_args()
     args.learned = args.legs in ("all", "learned")
     args.batched = args.legs in ("all", "batched")
+    args.ablation = args.legs in ("all", "ablation")
     if args.warmup < 3 and args.impl == "ours" and not os.environ.get("BENCH_ALLOW_SHORT"):
         args.warmup = 3
     if args.impl == "reference":
@@ -630,7 +683,10 @@ def main():
     if not args.no_cpu_baseline and rank == 0 and ws == 1:
         cpu = cpu_baseline(A)
 
-    learned_legs = batched = None
+    learned_legs = batched = ablation = None
+    if args.ablation and rank == 0:
+        ablation = hash_ablation_eval()
+        torch.cuda.empty_cache()
     if args.batched and rank == 0:
         batched = batched_eval()
         torch.cuda.empty_cache()
@@ -662,7 +718,7 @@ def main():
                 "roofline": roofline, "roofline_whole_step": whole,
                 "stage_ms_live": breakdown, "kernel_ms_serial": serial,
                 "bins": bins, "autotune": tuned, "numeric_values": rerun,
-                "learned": learned_legs, "batched": batched,
+                "learned": learned_legs, "batched": batched, "hash_access": ablation,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)

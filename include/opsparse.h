@@ -98,7 +98,13 @@ typedef void (*spgemm_free_fn)(void *ptr, void *stream, void *ctx);
  * the column space, so that the C.val lines being summed into stay in L2.
  * This halves that kernel's DRAM traffic on power-law inputs but executes
  * more instructions per product. window_entries: C entries per such window,
- * about (0 = 12288). */
+ * about (0 = 12288).
+ * hash_access: how a hash probe of the symbolic and numeric hash kernels
+ * reaches its slot. 0 (the default): one atomicCAS per probe, whose result
+ * is the slot's key (Sec. 5.6, Algorithms 4-5). 1: a plain read of the slot
+ * first and an atomicCAS only when the slot is empty, the access pattern of
+ * the libraries the paper compares its hashing against (Sec. 6). Results do
+ * not depend on it; it exists for that comparison. reserved must be 0. */
 typedef struct {
     int32_t sym_nbins;
     int32_t sym_kernel[SPGEMM_MAX_BINS];
@@ -111,7 +117,8 @@ typedef struct {
     int32_t bitmap_unroll;
     int32_t window_lists;
     int32_t window_entries;
-    int32_t reserved[3];
+    int32_t hash_access;
+    int32_t reserved[2];
 } spgemm_config;
 
 typedef struct spgemm_handle spgemm_handle;

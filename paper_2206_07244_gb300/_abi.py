@@ -61,7 +61,8 @@ class Config(ctypes.Structure):
                 ("num_range", ctypes.c_int64 * MAX_BINS),
                 ("lanes_per_brow", ctypes.c_int32), ("num_lanes_per_brow", ctypes.c_int32),
                 ("bitmap_unroll", ctypes.c_int32), ("window_lists", ctypes.c_int32),
-                ("window_entries", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("window_entries", ctypes.c_int32), ("hash_access", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -165,7 +166,8 @@ def config_to_dict(c: Config) -> dict:
             "lanes_per_brow": int(c.lanes_per_brow),
             "num_lanes_per_brow": int(c.num_lanes_per_brow),
             "bitmap_unroll": int(c.bitmap_unroll),
-            "window_lists": int(c.window_lists), "window_entries": int(c.window_entries)}
+            "window_lists": int(c.window_lists), "window_entries": int(c.window_entries),
+            "hash_access": int(c.hash_access)}
 
 
 def config_from_dict(d: dict) -> Config:
@@ -185,4 +187,5 @@ def config_from_dict(d: dict) -> Config:
     c.bitmap_unroll = int(d.get("bitmap_unroll", 0))
     c.window_lists = int(d.get("window_lists", 0))
     c.window_entries = int(d.get("window_entries", 0))
+    c.hash_access = int(d.get("hash_access", 0))
     return c

@@ -261,6 +261,8 @@ int validate_config(const spgemm_config &c) {
         return SPGEMM_ERR_INVALID;
     if (c.bitmap_unroll != 0 && c.bitmap_unroll != 4 && c.bitmap_unroll != 8) return SPGEMM_ERR_INVALID;
     if (c.window_lists < 0 || c.window_lists > kWinMaxLists || c.window_entries < 0) return SPGEMM_ERR_INVALID;
+    if (c.hash_access != 0 && c.hash_access != 1) return SPGEMM_ERR_INVALID;
+    if (c.reserved[0] != 0 || c.reserved[1] != 0) return SPGEMM_ERR_INVALID;
     for (int phase = 0; phase < 2; ++phase) {
         const int nb = phase ? c.num_nbins : c.sym_nbins;
         const int32_t *k = phase ? c.num_kernel : c.sym_kernel;
@@ -405,6 +407,7 @@ int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *s
         w.crpt = crpt; w.ccol = ccol; w.cval = cval;
         w.lanes = phase ? h->cfg.num_lanes_per_brow : h->cfg.lanes_per_brow;
         w.unroll = h->cfg.bitmap_unroll;
+        w.multi = h->cfg.hash_access;
         w.err = d_err(h);
         const KernelDesc &d = phase ? num_kernel(kid[j]) : sym_kernel(kid[j]);
         size_t smem = 0;

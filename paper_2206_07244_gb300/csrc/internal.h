@@ -45,6 +45,7 @@ struct BinWork {
     double *cval;         // numeric only
     int lanes;            // threads per B row, 0 = per-row automatic
     int unroll;           // bitmap kernels: products in flight per lane (4 or 8; 0 = 4)
+    int multi;            // plain hash kernels: read a slot before its compare-and-swap
     int *err;             // device error word
     // numeric bitmap kernel, pass 2 by column windows (B rows sorted)
     const int32_t *bs;    // run boundaries of B rows at the sub-ranges (G + 1 per row), or nullptr

@@ -28,14 +28,30 @@
 namespace ops {
 
 // Returns false when every slot holds another key (the table is full).
-template <int T>
+// MULTI: the access pattern the paper measures against (Sec. 6, the hashing
+// comparison), a plain read of the slot first and the compare-and-swap only
+// on an empty one; otherwise one access per probe (Algorithm 5).
+template <int T, bool MULTI = false>
 __device__ __forceinline__ bool num_insert(int *tk, double *tv, int key, double a, double b) {
     uint32_t h = hash_slot<T>(key);
     for (int it = 0; it < T; ++it) {
-        const int old = atomicCAS(tk + h, -1, key);
-        if (old == -1 || old == key) {
-            smem_fma_add(tv + h, a, b);
-            return true;
+        if (MULTI) {
+            const int cur = *static_cast<volatile int *>(tk + h);
+            bool hit = cur == key;
+            if (!hit && cur == -1) {
+                const int old = atomicCAS(tk + h, -1, key);
+                hit = old == -1 || old == key;
+            }
+            if (hit) {
+                smem_fma_add(tv + h, a, b);
+                return true;
+            }
+        } else {
+            const int old = atomicCAS(tk + h, -1, key);
+            if (old == -1 || old == key) {
+                smem_fma_add(tv + h, a, b);
+                return true;
+            }
         }
         h = next_slot<T>(h);
     }
@@ -131,7 +147,7 @@ __device__ __forceinline__ void warp_sort_store(const int *tk, const double *tv,
 // than the table can sort in place, marks the row as mispredicted: it is
 // queued for the exact path and nothing is written. Otherwise the row's
 // size goes to C.rpt and its sorted entries to its temporary slot.
-template <int TPR, int BLOCK, int T, bool ONE_PHASE = false>
+template <int TPR, int BLOCK, int T, bool ONE_PHASE = false, bool MULTI = false>
 __global__ void __launch_bounds__(BLOCK, (T * 12 * (BLOCK / TPR) > 110 * 1024) ? 1
                                          : ((TPR == 32 && T <= 256) ? 1536 : 2048) / BLOCK)
 num_hash_kernel(Operands op, BinWork w) {
@@ -171,11 +187,11 @@ num_hash_kernel(Operands op, BinWork w) {
         WalkScratch *sc = reinterpret_cast<WalkScratch *>(
             smem_raw + (sizeof(int) + sizeof(double)) * (size_t)RPB * T);
         block_row_walk<BLOCK, true>(op, p0, p1, S, sc, [&](int key, double a, double b) {
-            if (!num_insert<T>(tk, tv, key, a, b)) failed = true;
+            if (!num_insert<T, MULTI>(tk, tv, key, a, b)) failed = true;
         });
     } else {
         group_row_walk<TPR, true>(op, p0, p1, S, [&](int key, double a, double b) {
-            if (!num_insert<T>(tk, tv, key, a, b)) failed = true;
+            if (!num_insert<T, MULTI>(tk, tv, key, a, b)) failed = true;
         });
     }
     if (failed) {
@@ -723,6 +739,9 @@ static NumEntry g_num[] = {NUM_TABLE(NUM_ENTRY)};
 
 #define NUM_ONEPHASE_ENTRY(TPR, BLOCK, T) &num_hash_kernel<TPR, BLOCK, T, true>,
 static NumFn g_num_onephase[] = {NUM_TABLE(NUM_ONEPHASE_ENTRY)};
+// the plain kernels with the read-then-swap probe (BinWork::multi)
+#define NUM_MULTI_ENTRY(TPR, BLOCK, T) &num_hash_kernel<TPR, BLOCK, T, false, true>,
+static NumFn g_num_multi[] = {NUM_TABLE(NUM_MULTI_ENTRY)};
 static constexpr int kNumHash = sizeof(g_num) / sizeof(g_num[0]);
 static KernelDesc g_num_bitmap{1024, 1024, 0, LLONG_MAX, 1, 0};
 
@@ -752,6 +771,10 @@ cudaError_t num_prepare(int smem_optin) {
         cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(g_num_onephase[i]),
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(g_num[i].d.smem));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(reinterpret_cast<const void *>(g_num_multi[i]),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(g_num[i].d.smem));
         if (e != cudaSuccess) return e;
     }
     g_num_bitmap.table = static_cast<long long>((smem_optin - sizeof(WalkScratch)) / 12) * 64;
@@ -844,7 +867,8 @@ cudaError_t launch_num(int id, const Operands &op, const BinWork &w, size_t smem
         const KernelDesc &d = g_num[id].d;
         const int rpb = d.block / d.tpr;
         const int64_t grid = (w.cnt + rpb - 1) / rpb;
-        g_num[id].fn<<<static_cast<unsigned>(grid), d.block, d.smem, s>>>(op, w);
+        const NumFn fn = w.multi ? g_num_multi[id] : g_num[id].fn;
+        fn<<<static_cast<unsigned>(grid), d.block, d.smem, s>>>(op, w);
     } else {
         const int words = static_cast<int>(smem_bitmap / 12);
         BinWork wk = w;

@@ -28,13 +28,27 @@
 
 namespace ops {
 
-template <int T>
+// One access per probe (Algorithm 4): the compare-and-swap itself returns
+// the slot's key. MULTI: the access pattern the paper measures against
+// (Sec. 6, the hashing comparison), a plain read of the slot first and the
+// compare-and-swap only on an empty one.
+template <int T, bool MULTI = false>
 __device__ __forceinline__ int sym_insert(int *tab, int key, int *err) {
     uint32_t h = hash_slot<T>(key);
     for (int it = 0; it < T; ++it) {
-        const int old = atomicCAS(tab + h, -1, key);
-        if (old == -1) return 1;
-        if (old == key) return 0;
+        if (MULTI) {
+            const int cur = *static_cast<volatile int *>(tab + h);
+            if (cur == key) return 0;
+            if (cur == -1) {
+                const int old = atomicCAS(tab + h, -1, key);
+                if (old == -1) return 1;
+                if (old == key) return 0;
+            }
+        } else {
+            const int old = atomicCAS(tab + h, -1, key);
+            if (old == -1) return 1;
+            if (old == key) return 0;
+        }
         h = next_slot<T>(h);
     }
     set_error(err, DERR_TABLE_FULL);
@@ -44,7 +58,7 @@ __device__ __forceinline__ int sym_insert(int *tab, int key, int *err) {
 // Minimum resident blocks: enough for 2048 threads per SM (<= 32 registers
 // per thread, Sec. 5.6) unless the table is so large that one block fills
 // the SM's shared memory anyway.
-template <int TPR, int BLOCK, int T>
+template <int TPR, int BLOCK, int T, bool MULTI = false>
 __global__ void __launch_bounds__(BLOCK, (T * 4 * (BLOCK / TPR) > 110 * 1024) ? 1 : 2048 / BLOCK)
 sym_hash_kernel(Operands op, BinWork w) {
     constexpr int RPB = BLOCK / TPR;
@@ -67,7 +81,7 @@ sym_hash_kernel(Operands op, BinWork w) {
         const int64_t p1 = ld_rpt(op.arpt, op.a64, ar + 1);
         const int S = pick_lanes(w.lanes, w.crpt[row], p1 - p0, 32);
         block_row_walk<BLOCK, false>(op, p0, p1, S, sc, [&](int key, double, double) {
-            cnt += sym_insert<T>(tab, key, w.err);
+            cnt += sym_insert<T, MULTI>(tab, key, w.err);
         });
     } else {
         int64_t p0 = 0, p1 = 0;
@@ -81,7 +95,7 @@ sym_hash_kernel(Operands op, BinWork w) {
         // lanes of one group must agree on S: take the group's lane-0 value
         S = __shfl_sync(0xffffffffu, S, (threadIdx.x & 31) - lg);
         group_row_walk<TPR, false>(op, p0, p1, S, [&](int key, double, double) {
-            cnt += sym_insert<T>(tab, key, w.err);
+            cnt += sym_insert<T, MULTI>(tab, key, w.err);
         });
     }
     cnt = group_sum<TPR>(cnt, red);
@@ -147,6 +161,9 @@ struct SymEntry {
 
 static SymEntry g_sym[] = {SYM_TABLE(SYM_ENTRY)};
 static constexpr int kSymHash = sizeof(g_sym) / sizeof(g_sym[0]);
+// the same kernels with the read-then-swap probe (BinWork::multi)
+#define SYM_MULTI_ENTRY(TPR, BLOCK, T) &sym_hash_kernel<TPR, BLOCK, T, true>,
+static SymFn g_sym_multi[] = {SYM_TABLE(SYM_MULTI_ENTRY)};
 static KernelDesc g_sym_bitmap{1024, 1024, 0, LLONG_MAX, 1, 0};
 
 using BmFn = void (*)(Operands, BinWork, int);
@@ -169,6 +186,10 @@ cudaError_t sym_prepare(int smem_optin) {
         cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(g_sym[i].fn),
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(g_sym[i].d.smem));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(reinterpret_cast<const void *>(g_sym_multi[i]),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(g_sym[i].d.smem));
         if (e != cudaSuccess) return e;
     }
     g_sym_bitmap.table = static_cast<long long>((smem_optin - sizeof(WalkScratch)) / 4) * 32;
@@ -201,7 +222,8 @@ cudaError_t launch_sym(int id, const Operands &op, const BinWork &w, size_t smem
         const KernelDesc &d = g_sym[id].d;
         const int rpb = d.block / d.tpr;
         const int64_t grid = (w.cnt + rpb - 1) / rpb;
-        g_sym[id].fn<<<static_cast<unsigned>(grid), d.block, d.smem, s>>>(op, w);
+        const SymFn fn = w.multi ? g_sym_multi[id] : g_sym[id].fn;
+        fn<<<static_cast<unsigned>(grid), d.block, d.smem, s>>>(op, w);
     } else {
         const int words = static_cast<int>(smem_bitmap / 4);
         const size_t smem = smem_bitmap + sizeof(WalkScratch);

@@ -157,6 +157,22 @@ def contended_product(seed):
     return csr(a_rows, k), csr(b_rows, n)
 
 
+@pytest.mark.parametrize("phase", [0, 1])
+@pytest.mark.parametrize("kernel", range(len(ops.kernel_table(1)) - 1 if torch.cuda.is_available() else 0))
+def test_multi_access_probe_each_hash_kernel(phase, kernel):
+    # the read-then-swap probe (hash_access = 1, the access pattern the paper
+    # compares its hashing against) gives the same C in every hash kernel
+    A = W.rmat(11, 12, seed=71)
+    cfg = forced(phase, kernel)
+    cfg["hash_access"] = 1
+    with ops.Handle(cfg) as h:
+        check(A, A, gpu_product(A, A, h))
+    B = W.random_csr(300, 200, 0.05, seed=72, duplicates=True, unsorted=True, integer_values=True)
+    C = W.random_csr(200, 150, 0.08, seed=73, integer_values=True)
+    with ops.Handle(cfg) as h:
+        check(B, C, gpu_product(B, C, h), exact=True)
+
+
 @pytest.mark.parametrize("kernel", range(len(ops.kernel_table(1)) if torch.cuda.is_available() else 0))
 def test_contended_slot_updates_each_numeric_kernel(kernel):
     # every numeric kernel, many concurrent updates of one slot: the
