@@ -5,7 +5,12 @@ through the host-buffer C ABI call.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                     [--impl ours|reference] [--no-e2e] [--no-cpu-baseline]
-                    [--legs all|none|learned|batched]
+                    [--no-rerun] [--legs all|none|learned|batched|ablation]
+
+Besides the main line: the numeric phase run again over the kept structure
+with new values (spgemm_numeric_values), and the legs: learned sizing vs
+plain, 512 Galerkin products batched vs plain calls, and one-access vs
+read-then-swap hash probes on the 27-point stencil 128^3.
 
 Default workload: R-MAT n = 2^20, average degree 16 (a=.57, b=c=.19), seed 1,
 float64 values uniform in [-1, 1] (about 2.09e10 products, 9.7e9 entries in C,
