@@ -133,7 +133,7 @@ extern "C" int spgemm_rowptr_noalloc(const spgemm_csr_in *A, const spgemm_csr_in
     // symbolic kernels, largest rows first, all on the caller's stream
     for (int j = rs.nb - 1; j >= 0; --j) {
         if (size[j] <= 0) continue;
-        BinWork w;
+        BinWork w{};   // every field the symbolic kernels do not use stays zero (one-access probes)
         w.bins = identity ? nullptr : bins;
         w.off = identity ? 0 : off[j];
         w.cnt = size[j];
