@@ -104,7 +104,23 @@ typedef void (*spgemm_free_fn)(void *ptr, void *stream, void *ctx);
  * is the slot's key (Sec. 5.6, Algorithms 4-5). 1: a plain read of the slot
  * first and an atomicCAS only when the slot is empty, the access pattern of
  * the libraries the paper compares its hashing against (Sec. 6). Results do
- * not depend on it; it exists for that comparison. reserved must be 0. */
+ * not depend on it; it exists for that comparison.
+ * bitmap_path: how the last numeric bin (the rows past the hash tables) is
+ * computed. 0 (the default): when every row of B is sorted by column and B
+ * has at most 2^22 columns, each large row is cut into column windows that
+ * fit one block's shared memory, using per-cell entry counts that the
+ * symbolic bitmap kernel records; every window sums its products in shared
+ * memory (by column where the row is dense, by rank in a column bitmap
+ * elsewhere) and writes its part of the row once. The default configuration
+ * then also lowers the symbolic bitmap kernel's threshold so that every row
+ * with more entries than one whole-width window holds passes through it.
+ * Otherwise (unsorted B, wider B, or a configuration whose bins do not
+ * allow it) and with 1: one block per row with a bitmap of the whole column
+ * space, float64 sums in global memory. Results do not depend on it.
+ * window_budget: shared-memory bytes a column window may use for its
+ * accumulator, bitmap and ranks (0 = all that one block can have, the
+ * default). Smaller budgets cut rows into more, smaller windows; a budget
+ * too small for one fully dense cell turns the column windows off. */
 typedef struct {
     int32_t sym_nbins;
     int32_t sym_kernel[SPGEMM_MAX_BINS];
@@ -118,7 +134,8 @@ typedef struct {
     int32_t window_lists;
     int32_t window_entries;
     int32_t hash_access;
-    int32_t reserved[2];
+    int32_t bitmap_path;
+    int32_t window_budget;
 } spgemm_config;
 
 typedef struct spgemm_handle spgemm_handle;
@@ -232,6 +249,13 @@ int spgemm_multiply_host(spgemm_handle *h, const spgemm_csr_in *A,
  * or 1 (numeric bins): 3 * SPGEMM_MAX_BINS int64: rows per bin, sum of the
  * row sizes per bin (n_prod or n_nz), A entries of the bin's rows. */
 int spgemm_bin_stats(const spgemm_handle *h, int phase, int64_t *out, int n);
+
+/* Column windows of the last symbolic/numeric pair (see bitmap_path), up to
+ * 8 int64: 1 if the symbolic call prepared them, 1 if the numeric call ran
+ * them, windows, windows that accumulate by column, log2 of the cell width,
+ * cells per row, shared bytes per window, and the largest row size that
+ * takes one window over all columns. */
+int spgemm_window_stats(const spgemm_handle *h, int64_t *out, int n);
 
 /* Per-kernel timing with CUDA events recorded on the stream each kernel is
  * launched on. spgemm_kernel_times synchronises the handle's stream and

@@ -21,7 +21,8 @@ EXPORTS = [
     "spgemm_numeric", "spgemm_numeric_values", "spgemm_multiply", "spgemm_status", "spgemm_free",
     "spgemm_destroy", "spgemm_last_stats", "spgemm_kernel_info", "spgemm_strerror",
     "spgemm_last_cuda_error",
-    "spgemm_multiply_host", "spgemm_bin_stats", "spgemm_set_timing", "spgemm_kernel_times",
+    "spgemm_multiply_host", "spgemm_bin_stats", "spgemm_window_stats", "spgemm_set_timing",
+    "spgemm_kernel_times",
     "spgemm_rowptr_noalloc", "spgemm_mlp_param_count", "spgemm_set_predictor", "spgemm_set_mode",
     "spgemm_learned_stats", "spgemm_features", "spgemm_mlp_forward", "spgemm_mlp_train_step",
     "spgemm_mlp_adam", "spgemm_batch_create", "spgemm_batch_run", "spgemm_batch_sync",
@@ -62,7 +63,7 @@ class Config(ctypes.Structure):
                 ("lanes_per_brow", ctypes.c_int32), ("num_lanes_per_brow", ctypes.c_int32),
                 ("bitmap_unroll", ctypes.c_int32), ("window_lists", ctypes.c_int32),
                 ("window_entries", ctypes.c_int32), ("hash_access", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("bitmap_path", ctypes.c_int32), ("window_budget", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -102,6 +103,7 @@ def lib(path: str | None = None):
                                    ctypes.POINTER(I32), ctypes.POINTER(I64), ctypes.POINTER(I64)],
             "spgemm_multiply_host": [P, P, P, I64, SINK_FN, P, ctypes.POINTER(I64)],
             "spgemm_bin_stats": [P, ctypes.c_int, ctypes.POINTER(I64), ctypes.c_int],
+            "spgemm_window_stats": [P, ctypes.POINTER(I64), ctypes.c_int],
             "spgemm_set_timing": [P, ctypes.c_int],
             "spgemm_rowptr_noalloc": [P, P, P, P, ctypes.POINTER(I64)],
             "spgemm_mlp_param_count": [],
@@ -167,7 +169,8 @@ def config_to_dict(c: Config) -> dict:
             "num_lanes_per_brow": int(c.num_lanes_per_brow),
             "bitmap_unroll": int(c.bitmap_unroll),
             "window_lists": int(c.window_lists), "window_entries": int(c.window_entries),
-            "hash_access": int(c.hash_access)}
+            "hash_access": int(c.hash_access), "bitmap_path": int(c.bitmap_path),
+            "window_budget": int(c.window_budget)}
 
 
 def config_from_dict(d: dict) -> Config:
@@ -188,4 +191,6 @@ def config_from_dict(d: dict) -> Config:
     c.window_lists = int(d.get("window_lists", 0))
     c.window_entries = int(d.get("window_entries", 0))
     c.hash_access = int(d.get("hash_access", 0))
+    c.bitmap_path = int(d.get("bitmap_path", 0))
+    c.window_budget = int(d.get("window_budget", 0))
     return c

@@ -112,6 +112,23 @@ struct spgemm_handle {
     int64_t lstats[6 + kMaxBins] = {};  // one-phase rows, mispredicted rows, exact rows, temp
                                         // entries, rows > 3/4 full, rows that fit the next
                                         // smaller table, factor exponents used per class
+    // column-window numeric path for the last numeric bin (window.cu)
+    WinPlan wplan;                // plan of the last symbolic call
+    bool wp_on = false;           // the symbolic call prepared cell counts and a window count
+    uint16_t *wcells = nullptr;   // cell counts of the symbolic bitmap bin's rows
+    size_t wcells_bytes = 0;
+    int32_t *wcslot = nullptr;    // window row -> its index in the symbolic bitmap bin
+    size_t wcslot_bytes = 0;
+    long long nwin = 0;           // windows of the last symbolic call
+    long long nwin_col = 0;       // those that accumulate by column
+    // the last numeric call's windows and cell index of B, kept for
+    // spgemm_numeric_values while the structure is kept
+    Win *wlist = nullptr;
+    int32_t *wbslot = nullptr;
+    int32_t *wbidx = nullptr;
+    unsigned long long *wctr = nullptr;   // cursor, work counter, index slots
+    bool wkeep = false;
+    bool win_used = false;        // the last numeric call ran the column windows
     // per-kernel CUDA-event timing (off unless requested)
     // pinned staging for spgemm_multiply_host
     unsigned char *stage = nullptr;
@@ -262,7 +279,8 @@ int validate_config(const spgemm_config &c) {
     if (c.bitmap_unroll != 0 && c.bitmap_unroll != 4 && c.bitmap_unroll != 8) return SPGEMM_ERR_INVALID;
     if (c.window_lists < 0 || c.window_lists > kWinMaxLists || c.window_entries < 0) return SPGEMM_ERR_INVALID;
     if (c.hash_access != 0 && c.hash_access != 1) return SPGEMM_ERR_INVALID;
-    if (c.reserved[0] != 0 || c.reserved[1] != 0) return SPGEMM_ERR_INVALID;
+    if (c.bitmap_path != 0 && c.bitmap_path != 1) return SPGEMM_ERR_INVALID;
+    if (c.window_budget < 0) return SPGEMM_ERR_INVALID;
     for (int phase = 0; phase < 2; ++phase) {
         const int nb = phase ? c.num_nbins : c.sym_nbins;
         const int32_t *k = phase ? c.num_kernel : c.sym_kernel;
@@ -348,6 +366,85 @@ RunPlan run_plan(const spgemm_config &c, int smem_dyn_max, int64_t ncols) {
     return p;
 }
 
+// Column-window plan for the last numeric bin (window.cu), for B with
+// `ncols` columns. Cells of 2^cs columns, at most kWinMaxCells of them; a
+// window's accumulator, bitmap and ranks get the shared memory left after
+// the walk's head. Rows with more entries than a whole-width rank window
+// holds (e1) need the cell counts of the symbolic bitmap kernel, so every
+// such row must pass through it: the symbolic threshold must not exceed
+// max(numeric threshold, e1). The default configuration lowers it where
+// needed; an explicit configuration that breaks the rule keeps the
+// whole-row bitmap kernel. Returns false when the path is not used.
+bool win_setup(spgemm_handle *h, int64_t ncols) {
+    spgemm_config &c = h->cfg;
+    if (c.bitmap_path != 0 || ncols <= 0 || ncols > (int64_t{1} << kWinMaxColsLog2)) return false;
+    if (!num_kernel(c.num_kernel[c.num_nbins - 1]).bitmap || !sym_kernel(c.sym_kernel[c.sym_nbins - 1]).bitmap)
+        return false;
+    int lg = 0;
+    while ((int64_t{1} << lg) < ncols) ++lg;
+    WinPlan p;
+    p.cs = std::max(kWinMinCellLog2, lg - 8);
+    const int64_t cw = int64_t{1} << p.cs;
+    p.ncells = static_cast<int>((ncols + cw - 1) / cw);
+    p.ncols = ncols;
+    p.budget = ((static_cast<long long>(h->smem_dyn_max) - static_cast<long long>(win_head_bytes())) / 16) * 16;
+    if (c.window_budget > 0) p.budget = std::min<long long>(p.budget, (c.window_budget / 16) * 16);
+    if (p.ncells > kWinMaxCells || win_rank_bytes(cw, cw) > p.budget) return false;
+    p.kc = 0;
+    while (p.kc < p.ncells && win_col_bytes((p.kc + 1) * cw) <= p.budget) ++p.kc;
+    const long long room = p.budget - win_rank_bytes(ncols, 0);
+    p.e1 = room >= 8 ? std::min<long long>(room / 8 - 1, 65535) : -1;
+    p.cut = c.num_nbins >= 2 ? c.num_range[c.num_nbins - 2] : 0;
+    const long long lim = std::max(p.cut, p.e1);
+    if (c.sym_nbins >= 2 && c.sym_range[c.sym_nbins - 2] > lim) {
+        if (!h->cfg_auto) return false;
+        int keep = c.sym_nbins - 1;   // hash bins kept
+        while (keep > 1 && c.sym_range[keep - 1] > lim) --keep;
+        if (c.sym_range[keep - 1] > lim) return false;
+        c.sym_kernel[keep] = c.sym_kernel[c.sym_nbins - 1];
+        c.sym_range[keep] = -1;
+        c.sym_nbins = keep + 1;
+    }
+    h->wplan = p;
+    return true;
+}
+
+// Grow-only device buffer of the handle.
+template <typename T>
+int ensure_buf(spgemm_handle *h, T **p, size_t *have, size_t need) {
+    if (*p && *have >= need) return SPGEMM_OK;
+    dev_free(h, *p);
+    *p = static_cast<T *>(dev_alloc(h, need + need / 4));
+    *have = *p ? need + need / 4 : 0;
+    return *p ? SPGEMM_OK : SPGEMM_ERR_OOM;
+}
+
+// Drop the windows and B index kept for spgemm_numeric_values.
+void win_release(spgemm_handle *h) {
+    dev_free(h, h->wlist);
+    dev_free(h, h->wbslot);
+    dev_free(h, h->wbidx);
+    dev_free(h, h->wctr);
+    h->wlist = nullptr;
+    h->wbslot = nullptr;
+    h->wbidx = nullptr;
+    h->wctr = nullptr;
+    h->wkeep = false;
+}
+
+// What the numeric phase needs to run the last bin by column windows.
+struct WinCall {
+    bool on = false;
+    bool plan = true;          // build the B index and the window list first
+    WinWork ww{};
+    Win *list = nullptr;
+    long long cap = 0;
+    unsigned long long *cursor = nullptr, *nslot = nullptr;
+    int32_t *bslot = nullptr, *bidx = nullptr;
+    long long bcap = 0, min_len = 0;
+    int64_t brows = 0;
+};
+
 // Last CUDA runtime error the library turned into an error code on this
 // thread (spgemm_last_cuda_error).
 thread_local cudaError_t g_last_cuda = cudaSuccess;
@@ -391,7 +488,7 @@ Operands make_operands(const spgemm_csr_in *A, const spgemm_csr_in *B, int64_t r
 // numeric bitmap kernel (nullptr or runs->lists == 0: whole-row pass 2).
 int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *size,
              const long long *offset, bool identity, int64_t *crpt, int32_t *ccol, double *cval,
-             const RunPlan *runs = nullptr) {
+             const RunPlan *runs = nullptr, const WinCall *win = nullptr) {
     const int nb = phase ? h->cfg.num_nbins : h->cfg.sym_nbins;
     const int32_t *kid = phase ? h->cfg.num_kernel : h->cfg.sym_kernel;
     CK(cudaEventRecord(h->ev_fork, h->stream));
@@ -411,11 +508,36 @@ int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *s
         w.err = d_err(h);
         const KernelDesc &d = phase ? num_kernel(kid[j]) : sym_kernel(kid[j]);
         size_t smem = 0;
+        const int slot = (phase ? kSlotNumBin : kSlotSymBin) + j;
+        if (d.bitmap && phase == 1 && win && win->on) {
+            // column windows: index of B's long rows, the window list, then
+            // the persistent window kernel, one block per SM
+            time_begin(h, slot, s);
+            if (win->plan) {
+                CK(launch_win_bindex(op, win->brows, h->wplan, win->min_len, win->bslot, win->bidx, win->bcap,
+                                     win->nslot, s));
+                CK(launch_win_plan(h->wplan, w, h->wcells, h->wcslot, win->list, win->cap, win->cursor, s));
+            }
+            CK(launch_win_numeric(op, w, win->ww, h->sm_count, win_head_bytes() + static_cast<size_t>(win->ww.budget),
+                                  s));
+            time_end(h, slot, s);
+            ++used;
+            continue;
+        }
         if (d.bitmap) {
             // bitmap bytes; the kernels add their head (walk scratch / run metadata)
             if (phase == 0) {
                 const int64_t budget = h->smem_dyn_max - static_cast<int64_t>(sizeof(WalkScratch));
-                const int64_t words = std::min<int64_t>((op.ncols + 31) / 32, budget / 4);
+                int64_t words = std::min<int64_t>((op.ncols + 31) / 32, budget / 4);
+                if (win && win->on && h->wcells) {
+                    // per-cell counts: a pass covers whole cells
+                    const int64_t cwords = int64_t{1} << (h->wplan.cs - 5);
+                    if (words < (op.ncols + 31) / 32) words = (words / cwords) * cwords;
+                    w.cells = h->wcells;
+                    w.cslot = h->wcslot;
+                    w.cs = h->wplan.cs;
+                    w.ncells = h->wplan.ncells;
+                }
                 smem = static_cast<size_t>(std::max<int64_t>(words, 1)) * 4;
             } else {
                 const bool r = runs && runs->lists > 0 && runs->bs;
@@ -431,7 +553,6 @@ int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *s
                 smem = static_cast<size_t>(std::max<int64_t>(words, 1)) * 12;
             }
         }
-        const int slot = (phase ? kSlotNumBin : kSlotSymBin) + j;
         time_begin(h, slot, s);
         CK(phase ? launch_num(kid[j], op, w, smem, s) : launch_sym(kid[j], op, w, smem, s));
         time_end(h, slot, s);
@@ -735,7 +856,8 @@ int spgemm_create(spgemm_handle **out, const spgemm_config *cfg, spgemm_alloc_fn
         cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
         h->smem_dyn_max = optin - 1024;  // room for the kernels' static shared arrays
-        if (sym_prepare(h->smem_dyn_max) != cudaSuccess || num_prepare(h->smem_dyn_max) != cudaSuccess) {
+        if (sym_prepare(h->smem_dyn_max) != cudaSuccess || num_prepare(h->smem_dyn_max) != cudaSuccess ||
+            win_prepare(h->smem_dyn_max) != cudaSuccess) {
             rc = SPGEMM_ERR_CUDA;
             break;
         }
@@ -822,6 +944,11 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     const int64_t mw = row_end - row_begin;
     h->mw = mw;
     if (h->cfg_auto) auto_cut(h->cfg, B->cols);
+    win_release(h);
+    h->wp_on = h->mode == SPGEMM_MODE_PLAIN && win_setup(h, B->cols);
+    h->nwin = 0;
+    h->nwin_col = 0;
+    h->win_used = false;
     if ((rc = ensure_arena(h, mw))) return rc;
     int64_t *crpt = static_cast<int64_t *>(dev_alloc(h, sizeof(int64_t) * (size_t)(mw + 1)));
     if (!crpt) return SPGEMM_ERR_OOM;
@@ -863,7 +990,7 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     if (note(launch_nprod(op, crpt, h->sm_count * 8, h->stream)) != cudaSuccess) return fail(SPGEMM_ERR_CUDA);
     time_end(h, kSlotNprod, h->stream);
     h->rplan = run_plan(h->cfg, h->smem_dyn_max, B->cols);
-    if (h->rplan.lists > 0 &&
+    if ((h->rplan.lists > 0 || h->wp_on) &&
         note(launch_sorted_check(op, B->rows, B->nnz, d_counters(h, 1), h->sm_count * 4, h->stream)) !=
             cudaSuccess)
         return fail(SPGEMM_ERR_CUDA);
@@ -887,8 +1014,27 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
             return fail(SPGEMM_ERR_CUDA);
         time_end(h, kSlotSymPass2, h->stream);
     }
+    // cell counts of the symbolic bitmap bin's rows for the column windows
+    WinCall wc0;
+    if (h->wp_on) {
+        const long long nbm = ssize[rs.nb - 1];
+        if (nbm > 0 &&
+            ((rc = ensure_buf(h, &h->wcells, &h->wcells_bytes,
+                              sizeof(uint16_t) * (size_t)nbm * (size_t)h->wplan.ncells)) ||
+             (rc = ensure_buf(h, &h->wcslot, &h->wcslot_bytes, sizeof(int32_t) * (size_t)std::max<int64_t>(mw, 1)))))
+            return fail(rc);
+        if (nbm > 0 && note(cudaMemsetAsync(h->wcslot, 0xff, sizeof(int32_t) * (size_t)mw, h->stream)) != cudaSuccess)
+            return fail(SPGEMM_ERR_CUDA);
+        wc0.on = nbm > 0;
+    }
     // step 3: symbolic kernels, largest rows first
-    if ((rc = run_bins(h, 0, op, ssize, soff, sid, crpt, nullptr, nullptr))) return fail(rc);
+    if ((rc = run_bins(h, 0, op, ssize, soff, sid, crpt, nullptr, nullptr, nullptr, &wc0))) return fail(rc);
+    // windows of the rows of the last numeric bin (their count sizes the list)
+    if (h->wp_on &&
+        note(launch_win_count(h->wplan, crpt, mw, wc0.on ? h->wcells : nullptr, wc0.on ? h->wcslot : nullptr,
+                              &d_counters(h, 1)->windows, &d_counters(h, 1)->wcol, d_err(h), h->stream)) !=
+            cudaSuccess)
+        return fail(SPGEMM_ERR_CUDA);
     // step 4: numeric binning pass 1 -> total n_nz (and tile sums for the scan)
     Ranges rn{};
     rn.nb = h->cfg.num_nbins;
@@ -899,6 +1045,8 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     time_end(h, kSlotNumPass1, h->stream);
     if ((rc = read_counters(h))) return fail(rc);
     h->b_unsorted = (h->h_cnt[1].flags & 1ull) != 0;
+    h->nwin = static_cast<long long>(h->h_cnt[1].windows);
+    h->nwin_col = static_cast<long long>(h->h_cnt[1].wcol);
     h->stats[2] = static_cast<int64_t>(h->h_cnt[1].total);
     h->stats[3] = static_cast<int64_t>(h->h_cnt[1].max_size);
     for (int j = 0; j < SPGEMM_MAX_BINS; ++j)
@@ -992,6 +1140,45 @@ int spgemm_numeric(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in
         cval = static_cast<double *>(dev_alloc(h, sizeof(double) * (size_t)h->nnz));
         if (!ccol || !cval) return fail(SPGEMM_ERR_OOM);
     }
+    // column windows for the last bin
+    WinCall wc;
+    const int last = nb - 1;
+    if (h->wp_on && !h->b_unsorted && h->num_size[last] > 0 && h->nwin > 0 &&
+        num_kernel(h->cfg.num_kernel[last]).bitmap) {
+        win_release(h);
+        const WinPlan &p = h->wplan;
+        wc.on = true;
+        wc.min_len = std::max<long long>(32, (p.ncells + 1) / 2);
+        wc.bcap = B->nnz / wc.min_len + 1;
+        wc.brows = B->rows;
+        wc.cap = h->nwin;
+        h->wlist = static_cast<Win *>(dev_alloc(h, sizeof(Win) * (size_t)h->nwin));
+        h->wctr = static_cast<unsigned long long *>(dev_alloc(h, 4 * sizeof(unsigned long long)));
+        h->wbslot = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * (size_t)std::max<int64_t>(B->rows, 1)));
+        h->wbidx = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * (size_t)wc.bcap * (size_t)(p.ncells + 1)));
+        if (!h->wlist || !h->wctr || !h->wbslot || !h->wbidx) {
+            win_release(h);
+            return fail(SPGEMM_ERR_OOM);
+        }
+        if (note(cudaMemsetAsync(h->wctr, 0, 4 * sizeof(unsigned long long), h->stream)) != cudaSuccess) {
+            win_release(h);
+            return fail(SPGEMM_ERR_CUDA);
+        }
+        wc.list = h->wlist;
+        wc.cursor = h->wctr;
+        wc.nslot = h->wctr + 2;
+        wc.bslot = h->wbslot;
+        wc.bidx = h->wbidx;
+        wc.ww.win = h->wlist;
+        wc.ww.nwin = h->nwin;
+        wc.ww.next = h->wctr + 1;
+        wc.ww.bslot = h->wbslot;
+        wc.ww.bidx = h->wbidx;
+        wc.ww.cs = p.cs;
+        wc.ww.ncells = p.ncells;
+        wc.ww.budget = p.budget;
+        rp = RunPlan{};
+    }
     // run boundaries of B's rows at the column sub-ranges, for the windowed pass 2
     int32_t *bs = nullptr;
     if (rp.lists > 0) {
@@ -1004,9 +1191,14 @@ int spgemm_numeric(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in
         }
         rp.bs = bs;
     }
-    rc = run_bins(h, 1, op, h->num_size, off, nid, crpt, ccol, cval, &rp);
+    rc = run_bins(h, 1, op, h->num_size, off, nid, crpt, ccol, cval, &rp, &wc);
     dev_free(h, bs);
-    if (rc) return fail(rc);
+    if (rc) {
+        win_release(h);
+        return fail(rc);
+    }
+    h->wkeep = wc.on;
+    h->win_used = wc.on;
     h->reuse = true;
     h->reuse_arows = A->rows;
     h->reuse_annz = A->nnz;
@@ -1049,8 +1241,23 @@ int spgemm_numeric_values(spgemm_handle *h, const spgemm_csr_in *A, const spgemm
         nonempty += h->num_size[j] > 0;
     }
     const Operands op = make_operands(A, B, h->row0, h->mw);
+    // the last bin reuses the windows and B index of the numeric call
+    WinCall wc;
+    if (h->wkeep) {
+        wc.on = true;
+        wc.plan = false;
+        wc.ww.win = h->wlist;
+        wc.ww.nwin = h->nwin;
+        wc.ww.next = h->wctr + 1;
+        wc.ww.bslot = h->wbslot;
+        wc.ww.bidx = h->wbidx;
+        wc.ww.cs = h->wplan.cs;
+        wc.ww.ncells = h->wplan.ncells;
+        wc.ww.budget = h->wplan.budget;
+        CK(cudaMemsetAsync(h->wctr + 1, 0, sizeof(unsigned long long), h->stream));
+    }
     return run_bins(h, 1, op, h->num_size, off, nonempty <= 1, static_cast<int64_t *>(C->rpt), C->col,
-                    C->val, nullptr);
+                    C->val, nullptr, &wc);
 }
 
 int spgemm_multiply(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in *B,
@@ -1339,6 +1546,15 @@ int spgemm_bin_stats(const spgemm_handle *h, int phase, int64_t *out, int n) {
     return SPGEMM_OK;
 }
 
+int spgemm_window_stats(const spgemm_handle *h, int64_t *out, int n) {
+    if (!h || !out || n < 0) return SPGEMM_ERR_INVALID;
+    const int64_t v[8] = {h->wp_on ? 1 : 0, h->win_used ? 1 : 0, h->nwin, h->nwin_col,
+                          h->wp_on ? h->wplan.cs : 0, h->wp_on ? h->wplan.ncells : 0,
+                          h->wp_on ? h->wplan.budget : 0, h->wp_on ? h->wplan.e1 : 0};
+    for (int i = 0; i < std::min(n, 8); ++i) out[i] = v[i];
+    return SPGEMM_OK;
+}
+
 int spgemm_set_timing(spgemm_handle *h, int enable) {
     if (!h) return SPGEMM_ERR_INVALID;
     if (enable && !h->t0[0]) {
@@ -1408,6 +1624,9 @@ int spgemm_destroy(spgemm_handle *h) {
     dev_free(h, h->theta);
     dev_free(h, h->lscratch);
     dev_free(h, h->arena);
+    win_release(h);
+    dev_free(h, h->wcells);
+    dev_free(h, h->wcslot);
     if (h->side[0]) cudaStreamSynchronize(h->stream);
     for (int i = 0; i < kSide; ++i) {
         if (h->side[i]) cudaStreamDestroy(h->side[i]);

@@ -65,6 +65,11 @@ struct BinWork {
     const uint8_t *lcls;  // class of each window row (the bin of its prediction)
     unsigned long long *fb;   // load feedback counters (kFbCounters), or nullptr
     long long tprev;      // slots of the next smaller table (0: none)
+    // symbolic bitmap kernel: per-cell entry counts for the column-window
+    // numeric kernel (nullptr: not wanted)
+    uint16_t *cells;      // bin-local row r: cells[r * ncells + c] = entries in cell c
+    int32_t *cslot;       // window row -> its bin-local index in this bin
+    int cs, ncells;       // cells of 2^cs columns
 };
 
 struct Ranges {
@@ -81,6 +86,8 @@ struct Counters {
     unsigned long long max_size;
     unsigned long long total;
     unsigned long long flags;         // bit 0: some row of B has decreasing columns
+    unsigned long long windows;       // column windows of the large rows (win_count_kernel)
+    unsigned long long wcol;          // those of them that accumulate by column
 };
 
 // Windowed pass 2 of the numeric bitmap kernel: at most kWinMaxLists A
@@ -139,6 +146,69 @@ cudaError_t launch_bsplit(const Operands &op, int64_t brows, int64_t bnnz, int g
 // numeric.cu: shared bytes before the bitmap of num_bitmap_kernel (walk
 // scratch, or the run metadata of a windowed pass 2).
 size_t num_bitmap_head_bytes(bool runs);
+
+// --- window.cu -----------------------------------------------------------------
+// Column-window numeric kernel for the rows of the last numeric bin (the
+// large rows), used when every row of B is sorted. The column space is cut
+// into cells of 2^cs columns (at most kWinMaxCells); the symbolic bitmap
+// kernel counts each large row's entries per cell, and a planner cuts the
+// row into windows of whole cells that fit one block's shared memory:
+//   column window: a dense accumulator indexed by column (8 bytes per
+//                  column) plus a presence bitmap; one pass over the products;
+//   rank window:   a column bitmap with per-word ranks and an accumulator
+//                  indexed by rank (8 bytes per entry); two passes.
+// Rows with at most e1 entries take one rank window over all columns and need
+// no cell counts.
+constexpr int kWinMaxCells = 256;
+constexpr int kWinMinCellLog2 = 12;
+constexpr int kWinMaxColsLog2 = 22;
+enum : int { kWinRank = 0, kWinCol = 1 };
+
+struct WinPlan {
+    int cs = 0, ncells = 0;
+    long long ncols = 0;
+    long long budget = 0;   // shared bytes of a window's accumulator, bitmap and ranks
+    int kc = 0;             // cells of a column window, at most (0: no column windows)
+    long long e1 = -1;      // rows with at most e1 entries: one rank window
+    long long cut = 0;      // rows of the last numeric bin have more than `cut` entries
+};
+
+struct Win {
+    int32_t row;            // window row
+    int32_t c0, c1;         // columns [c0, c1)
+    int32_t mode;           // kWinRank / kWinCol
+    uint32_t r0;            // rank of the window's first entry in its row
+    uint32_t n;             // entries of the window
+};
+
+struct WinWork {
+    const Win *win;
+    long long nwin;
+    unsigned long long *next;      // work counter of the persistent kernel (zeroed)
+    const int32_t *bslot;          // B row -> slot of its cell index, or -1
+    const int32_t *bidx;           // slot s: (ncells + 1) offsets of the first entry of each cell
+    int cs, ncells;
+    long long budget;
+};
+
+long long win_rank_bytes(long long width, long long n);
+long long win_col_bytes(long long width);
+size_t win_head_bytes();
+cudaError_t win_prepare(int smem_optin);
+// Window count of each row of the window with more than plan.cut entries
+// (crpt holds n_nz), summed into *total.
+cudaError_t launch_win_count(const WinPlan &plan, const int64_t *crpt, int64_t mw, const uint16_t *cells,
+                             const int32_t *cslot, unsigned long long *total, unsigned long long *total_col,
+                             int *err, cudaStream_t s);
+// Cell index of the rows of B with at least `min_len` entries (slots up to cap).
+cudaError_t launch_win_bindex(const Operands &op, int64_t brows, const WinPlan &plan, long long min_len,
+                              int32_t *bslot, int32_t *bidx, long long cap, unsigned long long *nslot,
+                              cudaStream_t s);
+// Windows of the rows of bin w (crpt holds offsets), appended at *cursor.
+cudaError_t launch_win_plan(const WinPlan &plan, const BinWork &w, const uint16_t *cells, const int32_t *cslot,
+                            Win *list, long long cap, unsigned long long *cursor, cudaStream_t s);
+cudaError_t launch_win_numeric(const Operands &op, const BinWork &w, const WinWork &ww, int grid, size_t smem,
+                               cudaStream_t s);
 
 // --- batch.cu ------------------------------------------------------------------
 struct BatchProb {

@@ -118,6 +118,11 @@ sym_bitmap_kernel(Operands op, BinWork w, int words) {
     const int S = pick_lanes(w.lanes, w.crpt[row], p1 - p0, 32);
     const int64_t span = static_cast<int64_t>(words) * 32;
     long long total = 0;
+    // cell counts for the column-window numeric kernel: the pass span is a
+    // whole number of cells (the host rounds `words` down), so a cell never
+    // straddles two passes
+    uint16_t *cells = w.cells ? w.cells + static_cast<int64_t>(blockIdx.x) * w.ncells : nullptr;
+    if (w.cslot && threadIdx.x == 0) w.cslot[row] = static_cast<int32_t>(blockIdx.x);
     for (int64_t c0 = 0; c0 < op.ncols; c0 += span) {
         const int nw = static_cast<int>(((op.ncols - c0 < span ? op.ncols - c0 : span) + 31) / 32);
         for (int i = threadIdx.x; i < nw; i += kBmBlock) bm[i] = 0u;
@@ -128,7 +133,25 @@ sym_bitmap_kernel(Operands op, BinWork w, int words) {
             const unsigned rel = static_cast<unsigned>(key - c0i);   // one compare covers both ends
             if (rel < span32) atomicOr(bm + (rel >> 5), 1u << (rel & 31));
         });
-        for (int i = threadIdx.x; i < nw; i += kBmBlock) total += __popc(bm[i]);
+        if (cells) {
+            // one warp per cell: its words' bits, summed over the warp
+            const int cwords = 1 << (w.cs - 5);
+            const int ncp = (nw + cwords - 1) / cwords;
+            const int cell0 = static_cast<int>(c0 >> w.cs);
+            const int lane = threadIdx.x & 31;
+            for (int cc = threadIdx.x >> 5; cc < ncp; cc += kBmBlock / 32) {
+                const int e = (cc + 1) * cwords < nw ? (cc + 1) * cwords : nw;
+                unsigned v = 0;
+                for (int i = cc * cwords + lane; i < e; i += 32) v += __popc(bm[i]);
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) {
+                    total += v;
+                    if (cell0 + cc < w.ncells) cells[cell0 + cc] = static_cast<uint16_t>(v);
+                }
+            }
+        } else {
+            for (int i = threadIdx.x; i < nw; i += kBmBlock) total += __popc(bm[i]);
+        }
         __syncthreads();
     }
     total = group_sum<kBmBlock>(total, red);

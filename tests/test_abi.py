@@ -82,7 +82,8 @@ def test_config_dict_roundtrip():
     from paper_2206_07244_gb300 import _abi
     d = {"sym_kernel": [0, 9], "sym_range": [53, -1], "num_kernel": [2, 9],
          "num_range": [128, -1], "lanes_per_brow": 8, "num_lanes_per_brow": 32, "bitmap_unroll": 8,
-         "window_lists": 300, "window_entries": 4096, "hash_access": 1}
+         "window_lists": 300, "window_entries": 4096, "hash_access": 1, "bitmap_path": 1,
+         "window_budget": 65536}
     assert _abi.config_to_dict(_abi.config_from_dict(d)) == d
     with pytest.raises(ValueError):
         _abi.config_from_dict({"sym_kernel": [0], "sym_range": [], "num_kernel": [1],
