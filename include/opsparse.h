@@ -106,17 +106,24 @@ typedef void (*spgemm_free_fn)(void *ptr, void *stream, void *ctx);
  * the libraries the paper compares its hashing against (Sec. 6). Results do
  * not depend on it; it exists for that comparison.
  * bitmap_path: how the last numeric bin (the rows past the hash tables) is
- * computed. 0 (the default): when every row of B is sorted by column and B
- * has at most 2^22 columns, each large row is cut into column windows that
- * fit one block's shared memory, using per-cell entry counts that the
- * symbolic bitmap kernel records; every window sums its products in shared
- * memory (by column where the row is dense, by rank in a column bitmap
- * elsewhere) and writes its part of the row once. The default configuration
- * then also lowers the symbolic bitmap kernel's threshold so that every row
- * with more entries than one whole-width window holds passes through it.
- * Otherwise (unsorted B, wider B, or a configuration whose bins do not
- * allow it) and with 1: one block per row with a bitmap of the whole column
- * space, float64 sums in global memory. Results do not depend on it.
+ * computed. All forms give the same C.
+ *   0 (the default): one block per row with a column bitmap and its ranks
+ *     in shared memory, one window over the whole column space when it fits;
+ *     the values are summed in C.val by float64 L2 reductions.
+ *   1: the same, but when every row of B is sorted by column and B has at
+ *     most 2^22 columns a row is covered in column windows of about half an
+ *     SM's shared memory (two blocks per SM), each window walking only the
+ *     runs of B rows inside it, found in a cell index of B's long rows.
+ *     Unsorted B takes form 0.
+ *   2: rows cut into column windows planned from per-cell entry counts that
+ *     the symbolic bitmap kernel records, summed in shared memory (by column
+ *     where a window is dense, by rank elsewhere); needs sorted B and at most
+ *     2^22 columns, and lowers the symbolic bitmap kernel's threshold in the
+ *     default configuration so every row with more entries than one
+ *     whole-width window passes through it.
+ * On GB300 form 0 is the fastest on power-law inputs: the kernels are bound
+ * by the SM's rate of scattered L2 requests and float64 accumulation, which
+ * splitting rows does not raise (measured in the design notes).
  * window_budget: shared-memory bytes a column window may use for its
  * accumulator, bitmap and ranks (0 = all that one block can have, the
  * default). Smaller budgets cut rows into more, smaller windows; a budget
@@ -251,10 +258,11 @@ int spgemm_multiply_host(spgemm_handle *h, const spgemm_csr_in *A,
 int spgemm_bin_stats(const spgemm_handle *h, int phase, int64_t *out, int n);
 
 /* Column windows of the last symbolic/numeric pair (see bitmap_path), up to
- * 8 int64: 1 if the symbolic call prepared them, 1 if the numeric call ran
- * them, windows, windows that accumulate by column, log2 of the cell width,
- * cells per row, shared bytes per window, and the largest row size that
- * takes one window over all columns. */
+ * 9 int64. For bitmap_path 2: 1 if the symbolic call prepared them, 1 if the
+ * numeric call ran them, windows, windows that accumulate by column, log2 of
+ * the cell width, cells per row, shared bytes per window, and the largest
+ * row size that takes one window over all columns. Then 1 if the numeric
+ * call ran the default form's run-restricted windows (bitmap_path 0). */
 int spgemm_window_stats(const spgemm_handle *h, int64_t *out, int n);
 
 /* Per-kernel timing with CUDA events recorded on the stream each kernel is
@@ -387,6 +395,30 @@ int spgemm_batch_result(const spgemm_batch *b, int i, spgemm_csr_out *C);
 /* products, work items, blocks, lanes per row, table slots, rows per item */
 int spgemm_batch_info(const spgemm_batch *b, int64_t *out, int n);
 int spgemm_batch_destroy(spgemm_batch *b);
+
+/* ---- Operation-rate probes --------------------------------------------------
+ * Diagnostic, with no counterpart in the paper: the rates of the operations
+ * the numeric kernels are built from, which bound them beside the memory
+ * roofline. Every intermediate product costs one float64 multiply-add and
+ * one accumulation into its output entry. One 1024-thread block per SM runs
+ * `iters` operations per thread (after one untimed run); *gops receives
+ * operations per second / 1e9 (op 0: fused multiply-adds, two flops each).
+ *   op 0  float64 fma, 8 independent chains per thread
+ *   op 1  shared float64 accumulation by compare-and-swap of fma (the
+ *         kernels' update), over 16384 doubles
+ *   op 2  shared float64 atomicAdd over 16384 doubles
+ *   op 3  shared 32-bit atomicOr over 2^19 bits
+ *   op 4  shared 32-bit atomicCAS over 2^15 slots (a hash probe)
+ *   op 5  global float64 reduction (red.add) over at most 32 MB of buf
+ *         (L2-resident)
+ *   op 6  global float64 reduction over all of buf (mostly DRAM)
+ *   op 7  as op 5, but the 32 lanes of a warp reduce into 32 consecutive
+ *         doubles
+ * hot = 0 spreads the addresses uniformly; hot = h > 0 sends every
+ * operation to one of h addresses (contention). buf: device memory of
+ * buf_bytes (at least 1 MB) for ops 5 to 7, zeroed by the call; may be NULL
+ * otherwise. Synchronises `stream`. */
+int spgemm_probe(int op, int hot, int64_t iters, void *buf, int64_t buf_bytes, double *gops, void *stream);
 
 const char *spgemm_strerror(int code);
 /* Name of the last CUDA runtime error that the library, on the calling

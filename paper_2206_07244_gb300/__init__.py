@@ -246,11 +246,12 @@ class Handle:
                 "sym_bins": v[4:4 + MAX_BINS], "num_bins": v[4 + MAX_BINS:]}
 
     def window_stats(self) -> dict:
-        arr = (ctypes.c_int64 * 8)()
-        _abi.check(self._lib.spgemm_window_stats(self._h, arr, 8), "spgemm_window_stats")
+        arr = (ctypes.c_int64 * 9)()
+        _abi.check(self._lib.spgemm_window_stats(self._h, arr, 9), "spgemm_window_stats")
         v = list(arr)
         return {"planned": bool(v[0]), "used": bool(v[1]), "windows": v[2], "column_windows": v[3],
-                "cell_log2": v[4], "cells": v[5], "budget": v[6], "whole_width_max": v[7]}
+                "cell_log2": v[4], "cells": v[5], "budget": v[6], "whole_width_max": v[7],
+                "split": bool(v[8])}
 
     def status(self) -> None:
         _abi.check(self._lib.spgemm_status(self._h), "spgemm_status")

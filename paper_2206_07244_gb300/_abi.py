@@ -26,7 +26,7 @@ EXPORTS = [
     "spgemm_rowptr_noalloc", "spgemm_mlp_param_count", "spgemm_set_predictor", "spgemm_set_mode",
     "spgemm_learned_stats", "spgemm_features", "spgemm_mlp_forward", "spgemm_mlp_train_step",
     "spgemm_mlp_adam", "spgemm_batch_create", "spgemm_batch_run", "spgemm_batch_sync",
-    "spgemm_batch_result", "spgemm_batch_info", "spgemm_batch_destroy",
+    "spgemm_batch_result", "spgemm_batch_info", "spgemm_batch_destroy", "spgemm_probe",
 ]
 
 
@@ -113,6 +113,7 @@ def lib(path: str | None = None):
             "spgemm_batch_result": [P, ctypes.c_int, P],
             "spgemm_batch_info": [P, ctypes.POINTER(I64), ctypes.c_int],
             "spgemm_batch_destroy": [P],
+            "spgemm_probe": [ctypes.c_int, ctypes.c_int, I64, P, I64, ctypes.POINTER(ctypes.c_double), P],
             "spgemm_set_predictor": [P, P, ctypes.c_float],
             "spgemm_set_mode": [P, ctypes.c_int],
             "spgemm_learned_stats": [P, ctypes.POINTER(I64), ctypes.c_int],

@@ -127,8 +127,14 @@ struct spgemm_handle {
     int32_t *wbslot = nullptr;
     int32_t *wbidx = nullptr;
     unsigned long long *wctr = nullptr;   // cursor, work counter, index slots
+    double *wspill = nullptr;     // L2 spill of the window kernel's blocks (kept zero)
+    size_t wspill_bytes = 0;
     bool wkeep = false;
     bool win_used = false;        // the last numeric call ran the column windows
+    // whole-row bitmap kernel walked by half-width column windows (sorted B)
+    bool split_on = false;        // planned by the symbolic call
+    bool split_keep = false;      // the last numeric call used it (index kept)
+    int split_cs = 0, split_ncells = 0;
     // per-kernel CUDA-event timing (off unless requested)
     // pinned staging for spgemm_multiply_host
     unsigned char *stage = nullptr;
@@ -279,7 +285,7 @@ int validate_config(const spgemm_config &c) {
     if (c.bitmap_unroll != 0 && c.bitmap_unroll != 4 && c.bitmap_unroll != 8) return SPGEMM_ERR_INVALID;
     if (c.window_lists < 0 || c.window_lists > kWinMaxLists || c.window_entries < 0) return SPGEMM_ERR_INVALID;
     if (c.hash_access != 0 && c.hash_access != 1) return SPGEMM_ERR_INVALID;
-    if (c.bitmap_path != 0 && c.bitmap_path != 1) return SPGEMM_ERR_INVALID;
+    if (c.bitmap_path < 0 || c.bitmap_path > 2) return SPGEMM_ERR_INVALID;
     if (c.window_budget < 0) return SPGEMM_ERR_INVALID;
     for (int phase = 0; phase < 2; ++phase) {
         const int nb = phase ? c.num_nbins : c.sym_nbins;
@@ -377,7 +383,7 @@ RunPlan run_plan(const spgemm_config &c, int smem_dyn_max, int64_t ncols) {
 // whole-row bitmap kernel. Returns false when the path is not used.
 bool win_setup(spgemm_handle *h, int64_t ncols) {
     spgemm_config &c = h->cfg;
-    if (c.bitmap_path != 0 || ncols <= 0 || ncols > (int64_t{1} << kWinMaxColsLog2)) return false;
+    if (c.bitmap_path != 2 || ncols <= 0 || ncols > (int64_t{1} << kWinMaxColsLog2)) return false;
     if (!num_kernel(c.num_kernel[c.num_nbins - 1]).bitmap || !sym_kernel(c.sym_kernel[c.sym_nbins - 1]).bitmap)
         return false;
     int lg = 0;
@@ -392,8 +398,9 @@ bool win_setup(spgemm_handle *h, int64_t ncols) {
     if (p.ncells > kWinMaxCells || win_rank_bytes(cw, cw) > p.budget) return false;
     p.kc = 0;
     while (p.kc < p.ncells && win_col_bytes((p.kc + 1) * cw) <= p.budget) ++p.kc;
-    const long long room = p.budget - win_rank_bytes(ncols, 0);
-    p.e1 = room >= 8 ? std::min<long long>(room / 8 - 1, 65535) : -1;
+    // rows with at most e1 entries take one rank window over all columns
+    // (when its bitmap fits): too sparse for column windows to pay
+    p.e1 = win_rank_bytes(ncols, 0) <= p.budget ? kWinSingleMax : -1;
     p.cut = c.num_nbins >= 2 ? c.num_range[c.num_nbins - 2] : 0;
     const long long lim = std::max(p.cut, p.e1);
     if (c.sym_nbins >= 2 && c.sym_range[c.sym_nbins - 2] > lim) {
@@ -407,6 +414,24 @@ bool win_setup(spgemm_handle *h, int64_t ncols) {
     }
     h->wplan = p;
     return true;
+}
+
+// Whole-row numeric bitmap kernel by column windows: every row of the
+// last numeric bin is covered in windows of about half the shared memory of
+// an SM, so two blocks run per SM (one block's bitmap and C.col phases
+// overlap the other's float64 reductions), and with rows of B sorted each
+// window walks only the runs of B rows inside it (cell index of the long B
+// rows). Needs at most kWinMaxCells cells of 2^cs >= 2^12 columns.
+bool split_setup(spgemm_handle *h, int64_t ncols) {
+    const spgemm_config &c = h->cfg;
+    if (c.bitmap_path != 1 || ncols <= 0 || ncols > (int64_t{1} << kWinMaxColsLog2)) return false;
+    if (c.window_lists > 0 || !num_kernel(c.num_kernel[c.num_nbins - 1]).bitmap) return false;
+    int lg = 0;
+    while ((int64_t{1} << lg) < ncols) ++lg;
+    h->split_cs = std::max(kWinMinCellLog2, lg - 8);
+    const int64_t cw = int64_t{1} << h->split_cs;
+    h->split_ncells = static_cast<int>((ncols + cw - 1) / cw);
+    return h->split_ncells <= kWinMaxCells;
 }
 
 // Grow-only device buffer of the handle.
@@ -432,6 +457,18 @@ void win_release(spgemm_handle *h) {
     h->wkeep = false;
 }
 
+// L2 spill slots of the window kernel: one accumulator's worth per block,
+// zeroed when allocated; the kernel leaves every slot it uses zero.
+int ensure_spill(spgemm_handle *h, long long stride) {
+    const size_t need = sizeof(double) * static_cast<size_t>(stride) * static_cast<size_t>(h->sm_count);
+    if (h->wspill && h->wspill_bytes >= need) return SPGEMM_OK;
+    dev_free(h, h->wspill);
+    h->wspill = static_cast<double *>(dev_alloc(h, need));
+    h->wspill_bytes = h->wspill ? need : 0;
+    if (!h->wspill) return SPGEMM_ERR_OOM;
+    return cudaMemsetAsync(h->wspill, 0, need, h->stream) == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
+}
+
 // What the numeric phase needs to run the last bin by column windows.
 struct WinCall {
     bool on = false;
@@ -443,6 +480,9 @@ struct WinCall {
     int32_t *bslot = nullptr, *bidx = nullptr;
     long long bcap = 0, min_len = 0;
     int64_t brows = 0;
+    // whole-row bitmap kernel by half-width column windows over sorted B
+    bool split = false;
+    int cs = 0, ncells = 0;
 };
 
 // Last CUDA runtime error the library turned into an error code on this
@@ -548,8 +588,23 @@ int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *s
                     w.wlists = runs->lists;
                     w.wentries = runs->entries;
                 }
-                const int64_t budget = h->smem_dyn_max - static_cast<int64_t>(num_bitmap_head_bytes(r));
-                const int64_t words = std::min<int64_t>((op.ncols + 63) / 64, budget / 12);
+                int64_t budget = h->smem_dyn_max - static_cast<int64_t>(num_bitmap_head_bytes(r));
+                const bool split = !r && win && win->split;
+                if (split) {
+                    // half an SM's shared memory per block (two blocks per SM),
+                    // windows of whole cells
+                    budget = std::min<int64_t>(budget, (228 * 1024 - 2 * 1024) / 2 - 512 -
+                                                           static_cast<int64_t>(num_bitmap_head_bytes(false)));
+                    w.bslot = win->bslot;
+                    w.bidx = win->bidx;
+                    w.cs = win->cs;
+                    w.ncells = win->ncells;
+                }
+                int64_t words = std::min<int64_t>((op.ncols + 63) / 64, budget / 12);
+                if (split && words < (op.ncols + 63) / 64) {
+                    const int64_t cwords = int64_t{1} << (win->cs - 6);
+                    words = std::max<int64_t>(cwords, (words / cwords) * cwords);
+                }
                 smem = static_cast<size_t>(std::max<int64_t>(words, 1)) * 12;
             }
         }
@@ -946,6 +1001,8 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     if (h->cfg_auto) auto_cut(h->cfg, B->cols);
     win_release(h);
     h->wp_on = h->mode == SPGEMM_MODE_PLAIN && win_setup(h, B->cols);
+    h->split_on = h->mode == SPGEMM_MODE_PLAIN && split_setup(h, B->cols);
+    h->split_keep = false;
     h->nwin = 0;
     h->nwin_col = 0;
     h->win_used = false;
@@ -990,7 +1047,7 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     if (note(launch_nprod(op, crpt, h->sm_count * 8, h->stream)) != cudaSuccess) return fail(SPGEMM_ERR_CUDA);
     time_end(h, kSlotNprod, h->stream);
     h->rplan = run_plan(h->cfg, h->smem_dyn_max, B->cols);
-    if ((h->rplan.lists > 0 || h->wp_on) &&
+    if ((h->rplan.lists > 0 || h->wp_on || h->split_on) &&
         note(launch_sorted_check(op, B->rows, B->nnz, d_counters(h, 1), h->sm_count * 4, h->stream)) !=
             cudaSuccess)
         return fail(SPGEMM_ERR_CUDA);
@@ -1177,7 +1234,41 @@ int spgemm_numeric(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in
         wc.ww.cs = p.cs;
         wc.ww.ncells = p.ncells;
         wc.ww.budget = p.budget;
+        wc.ww.spill_stride = p.budget / 8;
+        if ((rc = ensure_spill(h, wc.ww.spill_stride))) {
+            win_release(h);
+            return fail(rc);
+        }
+        wc.ww.spill = h->wspill;
         rp = RunPlan{};
+    }
+    // whole-row bitmap kernel by column windows: cell index of B's long rows
+    if (!wc.on && h->split_on && !h->b_unsorted && h->num_size[last] > 0 && rp.lists == 0 &&
+        num_kernel(h->cfg.num_kernel[last]).bitmap) {
+        win_release(h);
+        wc.split = true;
+        wc.cs = h->split_cs;
+        wc.ncells = h->split_ncells;
+        wc.min_len = std::max<long long>(32, (h->split_ncells + 1) / 2);
+        wc.bcap = B->nnz / wc.min_len + 1;
+        h->wctr = static_cast<unsigned long long *>(dev_alloc(h, 4 * sizeof(unsigned long long)));
+        h->wbslot = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * (size_t)std::max<int64_t>(B->rows, 1)));
+        h->wbidx = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * (size_t)wc.bcap * (size_t)(wc.ncells + 1)));
+        if (!h->wctr || !h->wbslot || !h->wbidx) {
+            win_release(h);
+            return fail(SPGEMM_ERR_OOM);
+        }
+        WinPlan ip;
+        ip.cs = wc.cs;
+        ip.ncells = wc.ncells;
+        if (note(cudaMemsetAsync(h->wctr, 0, 4 * sizeof(unsigned long long), h->stream)) != cudaSuccess ||
+            note(launch_win_bindex(op, B->rows, ip, wc.min_len, h->wbslot, h->wbidx, wc.bcap, h->wctr + 2,
+                                   h->stream)) != cudaSuccess) {
+            win_release(h);
+            return fail(SPGEMM_ERR_CUDA);
+        }
+        wc.bslot = h->wbslot;
+        wc.bidx = h->wbidx;
     }
     // run boundaries of B's rows at the column sub-ranges, for the windowed pass 2
     int32_t *bs = nullptr;
@@ -1199,6 +1290,7 @@ int spgemm_numeric(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in
     }
     h->wkeep = wc.on;
     h->win_used = wc.on;
+    h->split_keep = wc.split;
     h->reuse = true;
     h->reuse_arows = A->rows;
     h->reuse_annz = A->nnz;
@@ -1254,7 +1346,15 @@ int spgemm_numeric_values(spgemm_handle *h, const spgemm_csr_in *A, const spgemm
         wc.ww.cs = h->wplan.cs;
         wc.ww.ncells = h->wplan.ncells;
         wc.ww.budget = h->wplan.budget;
+        wc.ww.spill_stride = h->wplan.budget / 8;
+        wc.ww.spill = h->wspill;
         CK(cudaMemsetAsync(h->wctr + 1, 0, sizeof(unsigned long long), h->stream));
+    } else if (h->split_keep) {
+        wc.split = true;
+        wc.cs = h->split_cs;
+        wc.ncells = h->split_ncells;
+        wc.bslot = h->wbslot;
+        wc.bidx = h->wbidx;
     }
     return run_bins(h, 1, op, h->num_size, off, nonempty <= 1, static_cast<int64_t *>(C->rpt), C->col,
                     C->val, nullptr, &wc);
@@ -1548,10 +1648,11 @@ int spgemm_bin_stats(const spgemm_handle *h, int phase, int64_t *out, int n) {
 
 int spgemm_window_stats(const spgemm_handle *h, int64_t *out, int n) {
     if (!h || !out || n < 0) return SPGEMM_ERR_INVALID;
-    const int64_t v[8] = {h->wp_on ? 1 : 0, h->win_used ? 1 : 0, h->nwin, h->nwin_col,
+    const int64_t v[9] = {h->wp_on ? 1 : 0, h->win_used ? 1 : 0, h->nwin, h->nwin_col,
                           h->wp_on ? h->wplan.cs : 0, h->wp_on ? h->wplan.ncells : 0,
-                          h->wp_on ? h->wplan.budget : 0, h->wp_on ? h->wplan.e1 : 0};
-    for (int i = 0; i < std::min(n, 8); ++i) out[i] = v[i];
+                          h->wp_on ? h->wplan.budget : 0, h->wp_on ? h->wplan.e1 : 0,
+                          h->split_keep ? 1 : 0};
+    for (int i = 0; i < std::min(n, 9); ++i) out[i] = v[i];
     return SPGEMM_OK;
 }
 
@@ -1627,6 +1728,7 @@ int spgemm_destroy(spgemm_handle *h) {
     win_release(h);
     dev_free(h, h->wcells);
     dev_free(h, h->wcslot);
+    dev_free(h, h->wspill);
     if (h->side[0]) cudaStreamSynchronize(h->stream);
     for (int i = 0; i < kSide; ++i) {
         if (h->side[i]) cudaStreamDestroy(h->side[i]);

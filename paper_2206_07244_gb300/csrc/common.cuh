@@ -358,9 +358,48 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned &total,
 // untouched in between (KEEP = 2) reuses the entries' B-row offsets, lengths,
 // A values and piece offsets when the row fits one chunk, instead of loading
 // them and scanning again.
-template <int BLOCK, bool NEED_VAL, int ITERS = kPieceIters, int KEEP = 0, typename F>
+// Restriction of a walk to the columns [c0, c1) of a window, for rows of B
+// sorted by column: each A entry's products are then one run of its B row,
+// found in the cell index of the long B rows (bidx, slot from bslot; offsets
+// of the first entry of each cell of 2^cs columns) or by binary search.
+struct RunSel {
+    const int32_t *bslot;
+    const int32_t *bidx;
+    int cs, ncells;
+    int c0, c1;
+};
+
+__device__ __forceinline__ long long lower_col_in(const int32_t *bcol, long long lo, long long hi, int c) {
+    while (lo < hi) {
+        const long long mid = lo + ((hi - lo) >> 1);
+        if (__ldg(bcol + mid) < c) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// [s, e) of B row k (entries [q0, q1)) inside the window's columns.
+__device__ __forceinline__ void run_in(const Operands &op, const RunSel &rs, int k, long long q0, long long q1,
+                                       long long &s, long long &e) {
+    s = q0;
+    e = q1;
+    if (rs.c0 <= 0 && rs.c1 >= op.ncols) return;
+    const int32_t slot = rs.bslot ? __ldg(rs.bslot + k) : -1;
+    if (slot >= 0) {
+        const int32_t *x = rs.bidx + static_cast<long long>(slot) * (rs.ncells + 1);
+        if (rs.c0 > 0) s = q0 + __ldg(x + (rs.c0 >> rs.cs));
+        if (rs.c1 < op.ncols) e = q0 + __ldg(x + (rs.c1 >> rs.cs));
+    } else {
+        if (rs.c0 > 0) s = lower_col_in(op.bcol, q0, q1, rs.c0);
+        if (rs.c1 < op.ncols) e = lower_col_in(op.bcol, s, q1, rs.c1);
+    }
+    if (e < s) e = s;
+}
+
+// RUNS: only the products inside the columns of *rs (rows of B sorted).
+template <int BLOCK, bool NEED_VAL, int ITERS = kPieceIters, int KEEP = 0, bool RUNS = false, typename F>
 __device__ __forceinline__ void block_row_walk(const Operands &op, int64_t p0, int64_t p1, int S,
-                                               WalkScratch *sc, F &&f) {
+                                               WalkScratch *sc, F &&f, const RunSel *rs = nullptr) {
     static_assert(BLOCK >= 32 && BLOCK % 32 == 0, "block walk needs whole warps");
     constexpr int CH = BLOCK < kWalkChunk ? BLOCK : kWalkChunk;
     const int nsub = BLOCK / S, sub = threadIdx.x / S, ls = threadIdx.x % S;
@@ -376,8 +415,14 @@ __device__ __forceinline__ void block_row_walk(const Operands &op, int64_t p0, i
                 const int t = threadIdx.x;
                 if (t < cnt) {
                     const int k = __ldg(op.acol + c + t);
-                    const long long q0 = ld_rpt(op.brpt, op.b64, k);
-                    const long long len = ld_rpt(op.brpt, op.b64, k + 1) - q0;
+                    long long q0 = ld_rpt(op.brpt, op.b64, k);
+                    long long len = ld_rpt(op.brpt, op.b64, k + 1) - q0;
+                    if (RUNS) {
+                        long long s0, e0;
+                        run_in(op, *rs, k, q0, q0 + len, s0, e0);
+                        q0 = s0;
+                        len = e0 - s0;
+                    }
                     sc->q0[t] = q0;
                     sc->len[t] = static_cast<int>(len);
                     if (NEED_VAL || KEEP == 1) sc->a[t] = __ldg(op.aval + c + t);

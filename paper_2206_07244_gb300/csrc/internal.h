@@ -70,6 +70,10 @@ struct BinWork {
     uint16_t *cells;      // bin-local row r: cells[r * ncells + c] = entries in cell c
     int32_t *cslot;       // window row -> its bin-local index in this bin
     int cs, ncells;       // cells of 2^cs columns
+    // numeric bitmap kernel over several column windows with rows of B
+    // sorted: cell index of the long B rows, so each window walks only its runs
+    const int32_t *bslot;
+    const int32_t *bidx;
 };
 
 struct Ranges {
@@ -155,14 +159,15 @@ size_t num_bitmap_head_bytes(bool runs);
 // row into windows of whole cells that fit one block's shared memory:
 //   column window: a dense accumulator indexed by column (8 bytes per
 //                  column) plus a presence bitmap; one pass over the products;
-//   rank window:   a column bitmap with per-word ranks and an accumulator
-//                  indexed by rank (8 bytes per entry); two passes.
+//   rank window:   a column bitmap with per-word ranks; one pass marks the
+//                  columns, a second adds the values into C.val in L2.
 // Rows with at most e1 entries take one rank window over all columns and need
 // no cell counts.
 constexpr int kWinMaxCells = 256;
 constexpr int kWinMinCellLog2 = 12;
 constexpr int kWinMaxColsLog2 = 22;
 enum : int { kWinRank = 0, kWinCol = 1 };
+constexpr long long kWinSingleMax = 16384;   // rows up to this size: one rank window
 
 struct WinPlan {
     int cs = 0, ncells = 0;
@@ -189,6 +194,10 @@ struct WinWork {
     const int32_t *bidx;           // slot s: (ncells + 1) offsets of the first entry of each cell
     int cs, ncells;
     long long budget;
+    // L2 spill of contended accumulations: block b owns spill[b * spill_stride ..),
+    // one double per accumulator entry, zero between windows
+    double *spill;
+    long long spill_stride;
 };
 
 long long win_rank_bytes(long long width, long long n);

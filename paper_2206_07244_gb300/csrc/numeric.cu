@@ -493,8 +493,11 @@ __device__ __forceinline__ void run_walk(const Operands &op, const RunMeta *rm, 
     }
 }
 
-template <int BLOCK, int ITERS>
-__global__ void __launch_bounds__(BLOCK, BLOCK == 1024 ? 1 : 1536 / BLOCK)
+// RUNS: the row is covered in several column windows and B's rows are
+// sorted; each window's passes walk only the runs of B rows inside it
+// (w.bslot / w.bidx), so a window costs its own products, not the row's.
+template <int BLOCK, int ITERS, bool RUNS = false>
+__global__ void __launch_bounds__(BLOCK, BLOCK == 1024 ? 1 : (RUNS ? 1024 : 1536) / BLOCK)
 num_bitmap_kernel(Operands op, BinWork w, int words) {
     constexpr int kBmBlock = BLOCK;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -529,10 +532,12 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
         // times slower on this GPU
         const int c0i = static_cast<int>(c0);
         const unsigned span32 = static_cast<unsigned>(span);
-        block_row_walk<kBmBlock, false, ITERS, 1>(op, p0, p1, S, sc, [&](int key, double, double) {
+        RunSel rsel{w.bslot, w.bidx, w.cs, w.ncells, c0i,
+                    static_cast<int>(c0 + span < op.ncols ? c0 + span : op.ncols)};
+        block_row_walk<kBmBlock, false, ITERS, 1, RUNS>(op, p0, p1, S, sc, [&](int key, double, double) {
             const unsigned rel = static_cast<unsigned>(key - c0i);   // one compare covers both ends
             if (rel < span32) atomicOr(bm32 + (rel >> 5), 1u << (rel & 31));
-        });
+        }, &rsel);
         // per-word prefix counts = rank of a word's first column in the
         // window. Warps own contiguous ranges of words and their lanes read
         // consecutive words (no bank conflicts): a warp scan per 32 words,
@@ -677,7 +682,7 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
             __syncthreads();
             // pass 2: each product lands on its column's rank (the walk
             // scratch of pass 1 is still in place)
-            block_row_walk<kBmBlock, true, ITERS, 2>(op, p0, p1, S, sc, [&](int key, double a, double b) {
+            block_row_walk<kBmBlock, true, ITERS, 2, RUNS>(op, p0, p1, S, sc, [&](int key, double a, double b) {
                 const unsigned rel = static_cast<unsigned>(key - c0i);
                 if (rel < span32) {
                     const unsigned wi = rel >> 6, bi = rel & 63u;
@@ -687,7 +692,7 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
                         static_cast<unsigned>(__popcll(bm[wi] << (63u - bi))) - 1u;
                     red_add_keep(cval + rank, a * b, pol);
                 }
-            });
+            }, &rsel);
             __syncthreads();
             // back to normal priority: every 128-byte line the segment touches
             const uintptr_t l0 = reinterpret_cast<uintptr_t>(cval) & ~static_cast<uintptr_t>(127);
@@ -751,6 +756,11 @@ static const struct { int block, iters; BmFn fn; } g_num_bm[] = {
     {1024, 4, &num_bitmap_kernel<1024, 4>}, {1024, 8, &num_bitmap_kernel<1024, 8>},
     {512, 4, &num_bitmap_kernel<512, 4>},   {256, 4, &num_bitmap_kernel<256, 4>},
 };
+// the same walked by column windows over sorted B (BinWork::bidx set): two
+// 512-thread blocks per SM when a window's bitmap takes half the SM
+static const struct { int block; BmFn fn; } g_num_bm_runs[] = {
+    {1024, &num_bitmap_kernel<1024, 4, true>}, {512, &num_bitmap_kernel<512, 4, true>},
+};
 
 int num_kernel_count() { return kNumHash + 1; }
 
@@ -779,6 +789,11 @@ cudaError_t num_prepare(int smem_optin) {
     }
     g_num_bitmap.table = static_cast<long long>((smem_optin - sizeof(WalkScratch)) / 12) * 64;
     for (const auto &v : g_num_bm) {
+        cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(v.fn),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        if (e != cudaSuccess) return e;
+    }
+    for (const auto &v : g_num_bm_runs) {
         cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(v.fn),
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
         if (e != cudaSuccess) return e;
@@ -875,6 +890,13 @@ cudaError_t launch_num(int id, const Operands &op, const BinWork &w, size_t smem
         wk.head = static_cast<int>(num_bitmap_head_bytes(w.bs != nullptr));
         if (!w.bs) wk.wlists = 0;
         const size_t smem = smem_bitmap + static_cast<size_t>(wk.head);
+        if (w.bidx && !w.bs) {
+            // two blocks per SM when two windows fit the SM's shared memory
+            const int two = (228 * 1024) / static_cast<int>(smem + 1024) >= 2;
+            const auto &v = g_num_bm_runs[two ? 1 : 0];
+            v.fn<<<static_cast<unsigned>(w.cnt), v.block, smem, s>>>(op, wk, words);
+            return cudaGetLastError();
+        }
         const auto &v = g_num_bm[pick_bitmap_variant(smem, w.unroll)];
         v.fn<<<static_cast<unsigned>(w.cnt), v.block, smem, s>>>(op, wk, words);
     }

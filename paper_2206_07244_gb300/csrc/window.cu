@@ -35,35 +35,84 @@
 namespace ops {
 
 constexpr int kWinBlock = 1024;
-constexpr int kWinCH = 256;     // A entries (runs) per chunk of the walk
 constexpr int kWinIters = 4;    // products one lane loads before using them
+constexpr int kWinBatch = 4;    // pieces a sub-group takes per grab of the piece counter
 
-// Shared bytes of a window's body.
-__host__ __device__ inline long long rank_bytes(long long width, long long n) {
+// Shared bytes of a window's body. A column window holds an accumulator
+// per column, presence bits, their ranks and spill bits; a rank window only a
+// bitmap of its columns and a 32-bit rank per 64-bit word (its values are
+// summed in C.val itself).
+__host__ __device__ inline long long rank_bytes(long long width, long long) {
     const long long nw = (width + 63) >> 6;
-    return ((8 * n + 15) & ~15LL) + 8 * nw + ((2 * nw + 15) & ~15LL);
+    return 12 * nw;
 }
 __host__ __device__ inline long long col_bytes(long long width) {
     const long long nw = (width + 31) >> 5;
-    return 8 * width + 8 * nw;   // accumulator, presence bits, ranks (width a multiple of 64)
+    return 8 * width + 12 * nw;   // accumulator, presence bits, ranks, spill bits
 }
 long long win_rank_bytes(long long width, long long n) { return rank_bytes(width, n); }
 long long win_col_bytes(long long width) { return col_bytes(width); }
 
 struct WinHead {
-    long long q[kWinCH];           // first B entry of each run
-    double a[kWinCH];              // A value of each run
-    int len[kWinCH];               // run length
-    long long pstart[kWinCH + 1];  // exclusive piece offsets
+    long long q[kWinBlock];          // first B entry of each run of the chunk
+    int len[kWinBlock];              // run length
+    int pstart[kWinBlock + 1];       // exclusive piece offsets
     long long red[34];
-    Win win;                       // the window being computed
+    Win win;                         // the window being computed
     long long widx;
-    int S;                         // threads per run of the current chunk
+    unsigned ctr;                    // piece counter of the chunk
+    int S;                           // threads per run of the current chunk
     int bad;
 };
 
 constexpr size_t kWinHeadBytes = (sizeof(WinHead) + 15) & ~static_cast<size_t>(15);
 size_t win_head_bytes() { return kWinHeadBytes; }
+
+// acc[idx[u]] += a * b[u] for the entries with idx[u] >= 0, in shared
+// memory, each with one compare-and-swap of the fused multiply-add. The
+// loads, multiply-adds and compare-and-swaps of the N entries are issued
+// together (no entry waits for another's round trip). A lost race (another
+// thread updated the entry in between, or the same entry twice in the
+// batch) does not retry: the product goes to the block's L2 spill slot
+// g[idx] with a float64 reduction, and the entry's spill bit is set. On a hot
+// entry (a column that many B rows share) shared-memory compare-and-swap
+// serialises on its round trip, while the L2 adds same-address reductions
+// in its own pipeline.
+template <int N>
+__device__ __forceinline__ void acc_add(double *acc, const int (&idx)[N], double a, const double (&b)[N], double *g,
+                                        unsigned *spill) {
+    unsigned long long *q = reinterpret_cast<unsigned long long *>(acc);
+    unsigned long long old[N], got[N];
+#pragma unroll
+    for (int u = 0; u < N; ++u) old[u] = idx[u] >= 0 ? q[idx[u]] : 0ull;
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+        got[u] = old[u];
+        if (idx[u] >= 0) {
+            const unsigned long long want = static_cast<unsigned long long>(
+                __double_as_longlong(fma(a, b[u], __longlong_as_double(static_cast<long long>(old[u])))));
+            got[u] = atomicCAS(q + idx[u], old[u], want);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+        if (idx[u] >= 0 && got[u] != old[u]) {
+            asm volatile("red.global.add.f64 [%0], %1;" ::"l"(g + idx[u]), "d"(a * b[u]) : "memory");
+            atomicOr(spill + (idx[u] >> 5), 1u << (idx[u] & 31));
+        }
+    }
+}
+
+// Value of accumulator entry i at the store: the shared sum plus, when its
+// spill bit is set, the L2 part, whose slot is cleared for the next window.
+__device__ __forceinline__ double acc_take(const double *acc, const unsigned *spill, double *g, unsigned i) {
+    double v = acc[i];
+    if ((spill[i >> 5] >> (i & 31)) & 1u) {
+        v += __ldcg(g + i);
+        __stcg(g + i, 0.0);
+    }
+    return v;
+}
 
 // --- planner -------------------------------------------------------------------
 // Cuts one row into windows; emit(c0, c1, r0, n, mode) for each. Returns
@@ -266,24 +315,27 @@ __device__ __forceinline__ long long block_sum_ll(long long x, long long *sw) {
     return t;
 }
 
-// Calls f(col, a_value, b_value) for every product of the current window:
+// Visits every product of the current window:
 // for each A entry of the row [p0, p1), the run of its B row inside columns
-// [c0, c1). Runs are read CH at a time; every run is cut into pieces of at
-// most S * ITERS products that the block's sub-groups of S lanes take in
-// equal contiguous ranges (coalesced reads of a run). keep: the row fits
-// one chunk and the previous walk of this window left its runs in place.
+// [c0, c1). Runs are set up BLOCK at a time (one per thread); every run is
+// cut into pieces of at most S * ITERS products, S the threads that read a
+// run together (from the chunk's mean run length, so short runs do not
+// leave lanes idle), and warps take pieces from a shared counter, a batch at
+// a time, so a warp that drew long runs does not hold the others at the
+// barrier. A lane loads its ITERS products, then hands them to
+// f(key[ITERS], a_value, b_value[ITERS]) together (key -1: no product).
+// keep: the row fits one chunk and the previous walk of this window left its
+// runs in place.
 template <int BLOCK, int ITERS, bool VAL, typename F>
 __device__ __forceinline__ void win_walk(const Operands &op, const WinWork &ww, int64_t p0, int64_t p1, int c0,
                                          int c1, WinHead *hd, bool keep, F &&f) {
-    constexpr int CH = kWinCH;
     const bool whole = c0 == 0 && c1 >= op.ncols;
-    for (int64_t c = p0; c < p1; c += CH) {
-        const int cnt = static_cast<int>(p1 - c < CH ? p1 - c : CH);
-        long long total;
-        int S;
-        if (keep && p1 - p0 <= CH) {
-            total = hd->pstart[CH];
-            S = hd->S;
+    const int lane = threadIdx.x & 31;
+    for (int64_t c = p0; c < p1; c += BLOCK) {
+        const int cnt = static_cast<int>(p1 - c < BLOCK ? p1 - c : BLOCK);
+        if (keep && p1 - p0 <= BLOCK) {
+            if (threadIdx.x == 0) hd->ctr = 0;
+            __syncthreads();
         } else {
             long long len = 0;
             if (threadIdx.x < cnt) {
@@ -306,68 +358,75 @@ __device__ __forceinline__ void win_walk(const Operands &op, const WinWork &ww, 
                 if (e < s) e = s;
                 hd->q[t] = s;
                 hd->len[t] = static_cast<int>(e - s);
-                hd->a[t] = __ldg(op.aval + c + t);
                 len = e - s;
             }
-            const long long sum = block_sum_ll(len, hd->red);
-            const int ne = __syncthreads_count(len > 0);
+            // mean length of the non-empty runs -> S (sum and count in one reduction)
+            const long long packed = block_sum_ll((len << 11) + (len > 0 ? 1 : 0), hd->red);
+            const long long ne = packed & 2047, sum = packed >> 11;
             const long long mean = ne ? (sum + ne - 1) / ne : 1;
-            S = 1;
+            int S = 1;
             while (S < 32 && static_cast<long long>(S) * ITERS < mean) S <<= 1;
             const long long W = static_cast<long long>(S) * ITERS;
-            const long long pieces = (len + W - 1) / W;
-            const long long ex = block_excl_scan_ll<BLOCK>(pieces, total, hd->red);
-            if (threadIdx.x < CH) hd->pstart[threadIdx.x] = ex;   // entries >= cnt hold `total`
+            long long total;
+            const long long ex = block_excl_scan_ll<BLOCK>((len + W - 1) / W, total, hd->red);
+            hd->pstart[threadIdx.x] = static_cast<int>(ex);   // entries >= cnt hold `total`
             if (threadIdx.x == 0) {
-                hd->pstart[CH] = total;
+                hd->pstart[BLOCK] = static_cast<int>(total);
                 hd->S = S;
+                hd->ctr = 0;
             }
             __syncthreads();
         }
-        const long long W = static_cast<long long>(S) * ITERS;
-        const int nsub = BLOCK / S, sub = threadIdx.x / S, ls = threadIdx.x % S;
-        const long long per = (total + nsub - 1) / nsub;
-        const long long it0 = per * sub;
-        const long long it1 = it0 + per < total ? it0 + per : total;
+        const int S = hd->S;
+        const int total = hd->pstart[BLOCK];
+        const int W = S * ITERS;
+        const int spw = 32 / S, wsub = lane / S, ls = lane % S;
+        const int a_off = static_cast<int>(c - p0);
         int lo = 0;
-        if (it0 < it1) {
-            int hi = cnt;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (hd->pstart[mid] <= it0) lo = mid; else hi = mid;
+        for (;;) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(&hd->ctr, static_cast<unsigned>(spw * kWinBatch));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base >= static_cast<unsigned>(total)) break;
+            const int it0 = static_cast<int>(base) + wsub * kWinBatch;
+            const int it1 = it0 + kWinBatch < total ? it0 + kWinBatch : total;
+            if (it0 >= it1) continue;
+            {   // last e with pstart[e] <= it0, at or after the previous one
+                int hi = cnt;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (hd->pstart[mid] <= it0) lo = mid; else hi = mid;
+                }
             }
-        }
-        long long next = hd->pstart[lo + 1];
-        for (long long it = it0; it < it1; ++it) {
-            while (it >= next) {
-                ++lo;
-                next = hd->pstart[lo + 1];
-            }
-            const long long piece = it - hd->pstart[lo];
-            const long long qb = hd->q[lo] + piece * W + ls;
-            const long long qe = hd->q[lo] + hd->len[lo];
-            const double a = VAL ? hd->a[lo] : 0.0;
-            int key[ITERS];
-            double bv[ITERS];
+            int next = hd->pstart[lo + 1];
+            for (int it = it0; it < it1; ++it) {
+                while (it >= next) {
+                    ++lo;
+                    next = hd->pstart[lo + 1];
+                }
+                const long long qb = hd->q[lo] + static_cast<long long>(it - hd->pstart[lo]) * W + ls;
+                const long long qe = hd->q[lo] + hd->len[lo];
+                const double a = VAL ? __ldg(op.aval + p0 + a_off + lo) : 0.0;
+                int key[ITERS];
+                double bv[ITERS];
 #pragma unroll
-            for (int u = 0; u < ITERS; ++u) {
-                const long long q = qb + static_cast<long long>(u) * S;
-                key[u] = q < qe ? __ldg(op.bcol + q) : -1;
-                bv[u] = (VAL && q < qe) ? __ldg(op.bval + q) : 0.0;
+                for (int u = 0; u < ITERS; ++u) {
+                    const long long q = qb + static_cast<long long>(u) * S;
+                    key[u] = q < qe ? __ldg(op.bcol + q) : -1;
+                    bv[u] = (VAL && q < qe) ? __ldg(op.bval + q) : 0.0;
+                }
+                f(key, a, bv);
             }
-#pragma unroll
-            for (int u = 0; u < ITERS; ++u)
-                if (key[u] >= 0) f(key[u], a, bv[u]);
         }
         __syncthreads();
     }
 }
 
-// Per-word ranks of a bitmap of nw 64-bit words as 16-bit counts (the
-// window holds fewer than 2^16 entries): pre[i] = set bits in words [0, i).
-// Warps own contiguous ranges of words, lanes read consecutive words.
+// Per-word ranks of a bitmap of nw 64-bit words: pre[i] = set bits in
+// words [0, i); returns the total. Warps own contiguous ranges of words,
+// lanes read consecutive words (no bank conflicts).
 template <int BLOCK>
-__device__ __forceinline__ unsigned ranks16(const unsigned long long *bm, uint16_t *pre, int nw, long long *sw) {
+__device__ __forceinline__ unsigned ranks32(const unsigned long long *bm, unsigned *pre, int nw, long long *sw) {
     constexpr int kWarps = BLOCK / 32;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int per = (((nw + kWarps - 1) / kWarps) + 31) & ~31;
@@ -387,7 +446,7 @@ __device__ __forceinline__ unsigned ranks16(const unsigned long long *bm, uint16
             const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
-        if (i < w1) pre[i] = static_cast<uint16_t>(base + inc - c);
+        if (i < w1) pre[i] = base + inc - c;
         base += __shfl_sync(0xffffffffu, inc, 31);
     }
     __syncthreads();
@@ -402,6 +461,7 @@ win_numeric_kernel(Operands op, BinWork w, WinWork ww) {
     unsigned char *body = smem_raw + kWinHeadBytes;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kWarps = BLOCK / 32;
+    double *gsp = ww.spill + static_cast<long long>(blockIdx.x) * ww.spill_stride;
     // the body starts zero; every window leaves it zero
     {
         uint4 *b4 = reinterpret_cast<uint4 *>(body);
@@ -430,32 +490,42 @@ win_numeric_kernel(Operands op, BinWork w, WinWork ww) {
         const unsigned uw = static_cast<unsigned>(width);
         bool bad = false;
         if (win.mode == kWinCol) {
-            // accumulator by column, then presence bits and their ranks
+            // accumulator by column, presence bits, their ranks, spill bits
             const int nw = static_cast<int>((width + 31) >> 5);
             double *acc = reinterpret_cast<double *>(body);
             unsigned *bits = reinterpret_cast<unsigned *>(body + 8 * width);
             unsigned *pre = bits + nw;
-            if (width <= 0 || col_bytes(width) > ww.budget) {
+            unsigned *spl = pre + nw;
+            if (width <= 0 || width > ww.spill_stride || col_bytes(width) > ww.budget) {
                 if (threadIdx.x == 0) set_error(w.err, DERR_WINDOW);
                 __syncthreads();
                 continue;
             }
-            win_walk<BLOCK, ITERS, true>(op, ww, p0, p1, c0, c1, hd, false, [&](int key, double a, double b) {
-                const unsigned rel = static_cast<unsigned>(key - c0);
-                if (rel < uw) {
-                    atomicOr(bits + (rel >> 5), 1u << (rel & 31));
-                    smem_fma_add(acc + rel, a, b);
-                } else {
-                    bad = true;
+            win_walk<BLOCK, ITERS, true>(op, ww, p0, p1, c0, c1, hd, false,
+                                         [&](const int (&key)[ITERS], double a, const double (&b)[ITERS]) {
+                int idx[ITERS];
+#pragma unroll
+                for (int u = 0; u < ITERS; ++u) {
+                    const unsigned rel = static_cast<unsigned>(key[u] - c0);
+                    idx[u] = -1;
+                    if (key[u] >= 0) {
+                        if (rel < uw) {
+                            atomicOr(bits + (rel >> 5), 1u << (rel & 31));
+                            idx[u] = static_cast<int>(rel);
+                        } else {
+                            bad = true;
+                        }
+                    }
                 }
+                acc_add<ITERS>(acc, idx, a, b, gsp, spl);
             });
             // ranks of the presence words: one word per thread, block scan
             long long tot = 0;
             for (int base = 0; base < nw; base += BLOCK) {
                 const int i = base + threadIdx.x;
-                const long long c = i < nw ? __popc(bits[i]) : 0;
+                const long long cb = i < nw ? __popc(bits[i]) : 0;
                 long long t;
-                const long long ex = block_excl_scan_ll<BLOCK>(c, t, hd->red);
+                const long long ex = block_excl_scan_ll<BLOCK>(cb, t, hd->red);
                 if (i < nw) pre[i] = static_cast<unsigned>(tot + ex);
                 tot += t;
             }
@@ -469,11 +539,12 @@ win_numeric_kernel(Operands op, BinWork w, WinWork ww) {
                 const unsigned x = bits[i];
                 if (!x) continue;
                 if ((x >> lane) & 1u) {
-                    const int rel = i * 32 + lane;
+                    const unsigned rel = static_cast<unsigned>(i * 32 + lane);
+                    const double v = acc_take(acc, spl, gsp, rel);
                     if (ok) {
                         const int64_t rk = out + pre[i] + __popc(x & lt);
-                        w.ccol[rk] = c0 + rel;
-                        w.cval[rk] = acc[rel];
+                        w.ccol[rk] = c0 + static_cast<int>(rel);
+                        w.cval[rk] = v;
                     }
                     acc[rel] = 0.0;
                 }
@@ -482,41 +553,43 @@ win_numeric_kernel(Operands op, BinWork w, WinWork ww) {
             for (int i = threadIdx.x; i < nw; i += BLOCK) {
                 bits[i] = 0u;
                 pre[i] = 0u;
+                spl[i] = 0u;
             }
         } else {
-            // rank window: bitmap, 16-bit ranks per word, accumulator by rank
+            // rank window: bitmap and 32-bit ranks per word; the values are
+            // summed into C.val itself with float64 L2 reductions (the
+            // entries of a sparse window rarely meet, so the L2 adds them
+            // without the round trips of shared-memory compare-and-swap)
             const int nw = static_cast<int>((width + 63) >> 6);
-            const long long acc_bytes = (8 * n + 15) & ~15LL;
-            double *acc = reinterpret_cast<double *>(body);
-            unsigned long long *bm = reinterpret_cast<unsigned long long *>(body + acc_bytes);
+            unsigned long long *bm = reinterpret_cast<unsigned long long *>(body);
             unsigned *bm32 = reinterpret_cast<unsigned *>(bm);
-            uint16_t *pre = reinterpret_cast<uint16_t *>(bm + nw);
-            if (width <= 0 || n > 65535 || rank_bytes(width, n) > ww.budget) {
+            unsigned *pre = reinterpret_cast<unsigned *>(bm + nw);
+            if (width <= 0 || rank_bytes(width, n) > ww.budget) {
                 if (threadIdx.x == 0) set_error(w.err, DERR_WINDOW);
                 __syncthreads();
                 continue;
             }
-            win_walk<BLOCK, ITERS, false>(op, ww, p0, p1, c0, c1, hd, false, [&](int key, double, double) {
-                const unsigned rel = static_cast<unsigned>(key - c0);
-                if (rel < uw) atomicOr(bm32 + (rel >> 5), 1u << (rel & 31));
-                else bad = true;
+            win_walk<BLOCK, ITERS, false>(op, ww, p0, p1, c0, c1, hd, false,
+                                          [&](const int (&key)[ITERS], double, const double (&)[ITERS]) {
+#pragma unroll
+                for (int u = 0; u < ITERS; ++u) {
+                    const unsigned rel = static_cast<unsigned>(key[u] - c0);
+                    if (key[u] < 0) continue;
+                    if (rel < uw) atomicOr(bm32 + (rel >> 5), 1u << (rel & 31));
+                    else bad = true;
+                }
             });
-            const unsigned tot = ranks16<BLOCK>(bm, pre, nw, hd->red);
+            const unsigned tot = ranks32<BLOCK>(bm, pre, nw, hd->red);
             const bool ok = tot == n;
             if (!ok && threadIdx.x == 0) set_error(w.err, DERR_COUNT_MISMATCH);
             if (ok) {
-                win_walk<BLOCK, ITERS, true>(op, ww, p0, p1, c0, c1, hd, true, [&](int key, double a, double b) {
-                    const unsigned rel = static_cast<unsigned>(key - c0);
-                    if (rel < uw) {
-                        const unsigned wi = rel >> 6, bi = rel & 63u;
-                        const unsigned rk = pre[wi] + static_cast<unsigned>(__popcll(bm[wi] << (63u - bi))) - 1u;
-                        if (rk < static_cast<unsigned>(n)) smem_fma_add(acc + rk, a, b);
-                    }
-                });
-                // store: each warp takes a contiguous range of words of about
-                // equal cost (entries + 2 per word); a lane writes its own
-                // word, words with many entries are written by the whole warp
-                // (lane = bit), so one store covers a run of entries
+                int32_t *ccol = w.ccol + out;
+                double *cval = w.cval + out;
+                const unsigned long long pol = l2_evict_last_policy();
+                // C.col in column order: each warp takes a contiguous range of
+                // words of about equal cost (entries + 2 per word); a lane
+                // writes its own word, words with many entries are written by
+                // the whole warp (lane = bit), so one store covers a run
                 constexpr int kDense = 24;
                 constexpr unsigned long long kWordCost = 2;
                 const unsigned lt = (1u << lane) - 1u;
@@ -533,8 +606,6 @@ win_numeric_kernel(Operands op, BinWork w, WinWork ww) {
                 const unsigned long long wq = static_cast<unsigned long long>(warp);
                 const int i_beg = first_word(vtot * wq / kWarps);
                 const int i_end = first_word(vtot * (wq + 1) / kWarps);
-                int32_t *ccol = w.ccol + out;
-                double *cval = w.cval + out;
                 for (int ib = i_beg; ib < i_end; ib += 32) {
                     const int i = ib + lane;
                     const unsigned long long x = i < i_end ? bm[i] : 0ull;
@@ -548,16 +619,12 @@ win_numeric_kernel(Operands op, BinWork w, WinWork ww) {
                         while (lo) {
                             const int b = __ffs(lo) - 1;
                             lo &= lo - 1;
-                            ccol[pos] = cb + b;
-                            cval[pos] = acc[pos];
-                            ++pos;
+                            ccol[pos++] = cb + b;
                         }
                         while (hi) {
                             const int b = __ffs(hi) - 1;
                             hi &= hi - 1;
-                            ccol[pos] = cb + 32 + b;
-                            cval[pos] = acc[pos];
-                            ++pos;
+                            ccol[pos++] = cb + 32 + b;
                         }
                     }
                     while (dm) {
@@ -567,25 +634,37 @@ win_numeric_kernel(Operands op, BinWork w, WinWork ww) {
                         const unsigned pw = __shfl_sync(0xffffffffu, pos0, src);
                         const int cb = c0 + (ib + src) * 64;
                         const unsigned lo = static_cast<unsigned>(xw), hi = static_cast<unsigned>(xw >> 32);
-                        if ((lo >> lane) & 1u) {
-                            const unsigned p = pw + __popc(lo & lt);
-                            ccol[p] = cb + lane;
-                            cval[p] = acc[p];
-                        }
-                        if ((hi >> lane) & 1u) {
-                            const unsigned p = pw + __popc(lo) + __popc(hi & lt);
-                            ccol[p] = cb + 32 + lane;
-                            cval[p] = acc[p];
-                        }
+                        if ((lo >> lane) & 1u) ccol[pw + __popc(lo & lt)] = cb + lane;
+                        if ((hi >> lane) & 1u) ccol[pw + __popc(lo) + __popc(hi & lt)] = cb + 32 + lane;
                     }
                 }
+                // C.val starts at zero; its lines stay in L2 (evict-last) while summed
+                for (long long t = threadIdx.x; t < n; t += BLOCK) st_keep(cval + t, 0.0, pol);
+                __syncthreads();
+                win_walk<BLOCK, ITERS, true>(op, ww, p0, p1, c0, c1, hd, true,
+                                             [&](const int (&key)[ITERS], double a, const double (&b)[ITERS]) {
+#pragma unroll
+                    for (int u = 0; u < ITERS; ++u) {
+                        const unsigned rel = static_cast<unsigned>(key[u] - c0);
+                        if (key[u] >= 0 && rel < uw) {
+                            const unsigned wi = rel >> 6, bi = rel & 63u;
+                            const unsigned rk = pre[wi] + static_cast<unsigned>(__popcll(bm[wi] << (63u - bi))) - 1u;
+                            if (rk < static_cast<unsigned>(n)) red_add_keep(cval + rk, a * b[u], pol);
+                        }
+                    }
+                });
+                // back to normal priority: every 128-byte line of the segment
+                const uintptr_t l0 = reinterpret_cast<uintptr_t>(cval) & ~static_cast<uintptr_t>(127);
+                const uintptr_t l1 = reinterpret_cast<uintptr_t>(cval + n);
+                for (uintptr_t l = l0 + 128 * static_cast<uintptr_t>(threadIdx.x); l < l1;
+                     l += 128 * static_cast<uintptr_t>(BLOCK))
+                    l2_priority_normal(reinterpret_cast<const void *>(l));
             }
             __syncthreads();
-            // leave the body zero: accumulator, bitmap and ranks
-            for (long long i = threadIdx.x; i < n; i += BLOCK) acc[i] = 0.0;
+            // leave the body zero: bitmap and ranks
             for (int i = threadIdx.x; i < nw; i += BLOCK) {
                 bm[i] = 0ull;
-                pre[i] = 0;
+                pre[i] = 0u;
             }
         }
         if (bad) hd->bad = 1;   // benign race: any writer sets 1

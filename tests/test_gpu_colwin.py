@@ -1,8 +1,12 @@
-"""GPU parity of the column-window path for the large rows (window.cu).
+"""GPU parity of the column-window forms of the large rows (the last numeric
+bin).
 
-Rows past the numeric hash tables are cut into column windows that are summed
-in shared memory: by column where a window is dense, by rank in a column
-bitmap elsewhere, and one window over all columns for rows small enough.
+bitmap_path 1: one block per row, two per SM, each row covered in column
+windows of half an SM's shared memory that walk only the runs of sorted B
+rows inside them. bitmap_path 2 (window.cu): rows cut into windows
+planned from per-cell counts and summed in shared memory, by column where a
+window is dense, by rank in a column bitmap elsewhere, one window over all
+columns for small rows.
 Every case is compared with the CPU oracle element by element (structure bit
 for bit, values within helpers.VALUE_RTOL, integer-valued inputs bit for
 bit), and window_stats() shows which kind of window ran, so each form is
@@ -26,7 +30,7 @@ import paper_2206_07244_gb300 as ops  # noqa: E402
 ops.build()
 
 
-def windows_only(budget=0, path=0):
+def windows_only(budget=0, path=2):
     """Every row to the symbolic and numeric bitmap bins (so every row has
     cell counts and every row of C goes through the window kernel)."""
     cfg = ops.default_config()
@@ -94,18 +98,21 @@ def test_whole_width_windows_rmat14():
     check(A, A, got)
 
 
-def test_small_budget_rank_and_column_windows_rmat16():
-    A = W.rmat(16, 16, seed=7)
-    got, st = run(A, A, windows_only(budget=40000))
-    assert st["used"] and st["column_windows"] > 0
-    nz = int(np.count_nonzero(oracle.symbolic(A, A)))
-    assert st["windows"] > st["column_windows"] + 0 and st["windows"] > nz
-    check(A, A, got)
+def test_small_budget_rank_and_column_windows_rmat18():
+    # a 40000-byte window holds a bitmap of 213K columns: no row of a 2^18-column
+    # product fits one window, so every row is planned from its cell counts,
+    # into column windows (dense cells) and rank windows (the rest)
+    A = W.rmat(18, 8, seed=7)
+    got, st = run(A, A, windows_only(budget=40000), 0, 4096)
+    assert st["used"] and st["whole_width_max"] == -1 and st["column_windows"] > 0
+    nz = int(np.count_nonzero(oracle.symbolic(A, A, 0, 4096)))
+    assert st["windows"] > st["column_windows"] and st["windows"] > nz
+    check(A, A, got, r0=0, r1=4096)
 
 
 def test_dense_rows_take_column_windows():
     A, B = wide_dense(48, 64, 1 << 20, 3000, 1 << 17, seed=11)
-    got, st = run(A, B)
+    got, st = run(A, B, windows_only())
     assert st["used"] and st["column_windows"] > 0
     check(A, B, got)
 
@@ -134,7 +141,7 @@ def test_integer_values_exact_laplacian():
 
 def test_row_window_of_heavy_rmat18_rows():
     A = W.rmat(18, 16, seed=9)
-    got, st = run(A, A, None, 0, 3000)
+    got, st = run(A, A, windows_only(), 0, 3000)
     assert st["used"] and st["windows"] > 0
     check(A, A, got, r0=0, r1=3000)
 
@@ -160,23 +167,24 @@ def test_unsorted_b_keeps_whole_row_kernel():
 
 def test_wide_b_keeps_whole_row_kernel():
     A, B = wide_dense(4, 8, 1 << 23, 500, 1 << 23, seed=15)
-    got, st = run(A, B)
+    got, st = run(A, B, windows_only())
     assert not st["planned"]
     check(A, B, got)
 
 
 def test_forced_whole_row_kernel_matches():
     A = W.rmat(15, 16, seed=16)
-    got, st = run(A, A, windows_only(path=1))
+    got, st = run(A, A, windows_only(path=0))
     assert not st["used"]
     check(A, A, got)
 
 
 def test_numeric_values_reuses_windows():
-    A = W.rmat(16, 16, seed=17)
+    A = W.rmat(18, 8, seed=17)
     with ops.Handle(windows_only(budget=40000)) as h:
         dA = dev(A)
-        C = h.multiply(dA, dA)
+        h.symbolic(dA, dA, 0, 4096)
+        C = h.numeric(dA, dA)
         st = h.window_stats()
         assert st["used"] and st["column_windows"] > 0
         rng = np.random.default_rng(3)
@@ -184,4 +192,76 @@ def test_numeric_values_reuses_windows():
             A2 = W.Csr(A.rows, A.cols, A.rpt, A.col, rng.uniform(-2, 2, A.nnz))
             C2 = h.numeric_values(dev(A2), dev(A2), C)
             h.status()
-            check(A2, A2, C2.numpy())
+            check(A2, A2, C2.numpy(), r0=0, r1=4096)
+
+
+# --- the default form: run-restricted half-width windows, two blocks per SM ---
+
+def bitmap_bin_only(path=1):
+    """Every row of C to the numeric bitmap kernel, default symbolic bins."""
+    cfg = ops.default_config()
+    nb = len(ops.kernel_table(1)) - 1
+    cfg["num_kernel"], cfg["num_range"] = [nb], [-1]
+    cfg["bitmap_path"] = path
+    return cfg
+
+
+def test_split_windows_wide_rows():
+    # 2^20 columns: two windows per row, the second found through the index
+    A, B = wide_dense(48, 64, 1 << 20, 3000, 1 << 20, seed=21)
+    got, st = run(A, B, bitmap_bin_only())
+    assert st["split"]
+    check(A, B, got)
+
+
+def test_split_windows_many_windows_and_duplicates():
+    # 3M columns: six windows per row; B rows with repeated columns
+    A, B = wide_dense(12, 40, 3_000_000, 8000, 3_000_000, seed=22, dup=True)
+    got, st = run(A, B, bitmap_bin_only())
+    assert st["split"]
+    check(A, B, got)
+
+
+def test_split_single_window_rmat16_every_row():
+    A = W.rmat(16, 16, seed=23)
+    got, st = run(A, A, bitmap_bin_only())
+    assert st["split"]
+    check(A, A, got)
+
+
+def test_split_integer_values_exact():
+    A = W.laplacian_2d(64)
+    got, st = run(A, A, bitmap_bin_only())
+    assert st["split"]
+    check(A, A, got, exact=True)
+
+
+def test_split_unsorted_b_takes_whole_width():
+    A, B = wide_dense(16, 32, 1 << 20, 2000, 1 << 20, seed=24)
+    col = B.col.copy()
+    col[B.rpt[5]:B.rpt[6]] = col[B.rpt[5]:B.rpt[6]][::-1]
+    B2 = W.Csr(B.rows, B.cols, B.rpt, col, B.val.copy())
+    got, st = run(A, B2, bitmap_bin_only())
+    assert not st["split"]
+    check(A, B2, got)
+
+
+def test_default_path_is_whole_width():
+    A, B = wide_dense(16, 32, 1 << 20, 2000, 1 << 20, seed=25)
+    got, st = run(A, B, bitmap_bin_only(path=0))
+    assert not st["split"]
+    check(A, B, got)
+
+
+def test_split_numeric_values_rerun():
+    A, B = wide_dense(24, 48, 1 << 20, 2500, 1 << 20, seed=26)
+    with ops.Handle(bitmap_bin_only()) as h:
+        dA, dB = dev(A), dev(B)
+        C = h.multiply(dA, dB)
+        assert h.window_stats()["split"]
+        rng = np.random.default_rng(5)
+        for _ in range(2):
+            B2 = W.Csr(B.rows, B.cols, B.rpt, B.col, rng.uniform(-2, 2, B.nnz))
+            C2 = h.numeric_values(dA, dev(B2), C)
+            h.status()
+            check(A, B2, C2.numpy())
