@@ -64,11 +64,50 @@ SLOT_NAMES = ([f"sym_bin{j}" for j in range(16)] + [f"num_bin{j}" for j in range
 NSLOTS = len(SLOT_NAMES)
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
-# of a workload's dominant kernel, from an ncu capture of this code (summary
-# and command in profiles/); None where no capture of the current kernel
-# exists.
-TRAFFIC = {("rmat20", "num_bitmap_kernel"): 235_366_154_496 + 212_000_421_888}
+# DRAM traffic of the dominant kernel, from an ncu capture of a row window of
+# the workload (dram__bytes_read.sum + dram__bytes_write.sum of that launch),
+# scaled to a whole launch by the window's share of the kernel's
+# intermediate products. Each entry records the hash of the kernel sources at
+# capture time; a kernel changed since then reports no traffic.
+TRAFFIC_WINDOWED = {
+    # ("rmat20", "num_bitmap_kernel"): {"rows": "R0:R1", "dram_bytes": B,
+    #     "window_products": P, "sources_sha": "..."},
+}
+KERNEL_SOURCES = ["paper_2206_07244_gb300/csrc/numeric.cu", "paper_2206_07244_gb300/csrc/common.cuh"]
+
+
+def kernel_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def op_rates(lib):
+    """Rates of the operations a product costs, measured now (spgemm_probe):
+    float64 fma, shared-memory float64 accumulation by compare-and-swap,
+    float64 L2 reductions scattered (one address per lane) and coalesced (a
+    warp's 32 lanes on 32 consecutive doubles), and reductions over 1 GB."""
+    import ctypes
+
+    import torch
+    from paper_2206_07244_gb300 import _abi
+    buf = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, op, it in (("fp64_fma_gops", 0, 8192), ("smem_cas_fma_gops", 1, 32768),
+                         ("l2_red_scattered_gops", 5, 32768), ("l2_red_coalesced_gops", 7, 65536),
+                         ("dram_red_scattered_gops", 6, 4096), ("smem_or_u32_gops", 3, 131072)):
+        g = ctypes.c_double()
+        _abi.check(lib.spgemm_probe(op, 0, it, ctypes.c_void_p(buf.data_ptr()), buf.numel(),
+                                    ctypes.byref(g), None), "spgemm_probe")
+        out[name] = round(g.value, 2)
+    del buf
+    torch.cuda.empty_cache()
+    out["what"] = ("one 1024-thread block per SM, uniform random addresses (fma: 8 independent "
+                   "chains per thread); Gop/s")
+    return out
 
 
 def peaks():
@@ -405,6 +444,161 @@ def hash_ablation_eval(reps=3):
             "num_speedup_single_over_multi": round(res[1]["num_hash_ms"] / max(res[0]["num_hash_ms"], 1e-9), 3)}
 
 
+def _kernel_bytes(bins_sym, bins_num, k, b_bytes):
+    """Algorithmic bytes of bin kernel k (slot index) in one multiply: its
+    A rows, the referenced B rows (b_bytes, the whole product's) and its
+    output (C rows for a numeric bin, 16 bytes per row for a symbolic one)."""
+    phase, j = divmod(k, 16)
+    bs = list(bins_num if phase else bins_sym)
+    rows_j, size_j, nnza_j = bs[j], bs[16 + j], bs[32 + j]
+    return 8 * rows_j + 12 * nnza_j + b_bytes + ((16 * rows_j + 12 * size_j) if phase else 16 * rows_j)
+
+
+def nprod_rows(A):
+    rpt = A.rpt.astype(np.int64)
+    cs = np.concatenate([[0], np.cumsum(np.diff(rpt)[A.col])])
+    return cs[rpt[1:]] - cs[rpt[:-1]]
+
+
+def slabs_by_products(A, per_slab):
+    """Contiguous row slabs of A*A with about per_slab products each."""
+    csum = np.concatenate([[0], np.cumsum(nprod_rows(A))])
+    cuts = [0]
+    while cuts[-1] < A.rows:
+        r = int(np.searchsorted(csum, csum[cuts[-1]] + per_slab, side="right")) - 1
+        cuts.append(min(A.rows, max(r, cuts[-1] + 1)))
+    return list(zip(cuts[:-1], cuts[1:]))
+
+
+def config_line(name, A, slabs, cfg=None, learned_theta=None, margin=0.0, warm=1, note=None):
+    """One whole multiply of A*A as a sequence of row slabs (one slab = the
+    whole matrix when it fits): CUDA-event time of a pass over all slabs after
+    `warm` untimed passes, GFLOPS, the dominant kernel (longest summed over
+    the slabs with every kernel serialised on one stream, one more pass) and
+    its fraction of the measured copy bandwidth, and the whole pass's
+    compulsory-byte fraction."""
+    import ctypes
+
+    import torch
+
+    import paper_2206_07244_gb300 as ops
+    from paper_2206_07244_gb300 import _abi
+    lib = _abi.lib()
+    peak, peak_kind = peaks()
+    dA = ops.CSR.from_workload(A)
+    h = ops.Handle(cfg)
+    if learned_theta is not None:
+        h.set_predictor(learned_theta, margin)
+        h.set_mode("learned")
+
+    def one_pass():
+        for r0, r1 in slabs:
+            h.symbolic(dA, dA, r0, r1)
+            C = h.numeric(dA, dA)
+            del C
+
+    for _ in range(warm):
+        one_pass()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    one_pass()
+    e1.record(s)
+    h.status()
+    ms = e0.elapsed_time(e1)
+    # serialised per-kernel times and bin statistics, summed over the slabs
+    ms_arr = (ctypes.c_double * NSLOTS)()
+    ln_arr = (ctypes.c_int64 * NSLOTS)()
+    _abi.check(lib.spgemm_set_timing(h._h, 2), "spgemm_set_timing")
+    _abi.check(lib.spgemm_kernel_times(h._h, ms_arr, ln_arr, NSLOTS, 1), "spgemm_kernel_times")
+    nprod = nnz = 0
+    kbytes = {}
+    total_bytes = 0
+    slot_ms = np.zeros(NSLOTS)
+    for r0, r1 in slabs:
+        h.symbolic(dA, dA, r0, r1)
+        C = h.numeric(dA, dA)
+        del C
+        _abi.check(lib.spgemm_kernel_times(h._h, ms_arr, ln_arr, NSLOTS, 1), "spgemm_kernel_times")
+        slot_ms += np.array(list(ms_arr))
+        st = h.stats()
+        nprod += st["total_nprod"]
+        nnz += st["total_nnz"]
+        bins_sym = (ctypes.c_int64 * 48)()
+        bins_num = (ctypes.c_int64 * 48)()
+        lib.spgemm_bin_stats(h._h, 0, bins_sym, 48)
+        lib.spgemm_bin_stats(h._h, 1, bins_num, 48)
+        tb, b_bytes = compulsory_bytes(A, r0, r1, st["total_nnz"])
+        total_bytes += tb
+        for k in range(32):
+            kbytes[k] = kbytes.get(k, 0) + _kernel_bytes(bins_sym, bins_num, k, b_bytes)
+    lib.spgemm_set_timing(h._h, 0)
+    lstats = h.learned_stats() if learned_theta is not None else None
+    h.close()
+    del dA
+    torch.cuda.empty_cache()
+    k = int(np.argmax(slot_ms[:32]))
+    kb = kbytes[k]
+    kgbs = kb / (slot_ms[k] / 1e3) / 1e9
+    wgbs = total_bytes / (ms / 1e3) / 1e9
+    out = {"config": name, "slabs": len(slabs), "ms": round(ms, 3), "nprod": int(nprod), "nnzC": int(nnz),
+           "gflops": round(2.0 * nprod / (ms / 1e3) / 1e9, 3),
+           "dominant_kernel": SLOT_NAMES[k], "dominant_kernel_ms_serial": round(float(slot_ms[k]), 3),
+           "dominant_kernel_share_serial": round(float(slot_ms[k] / max(slot_ms[:38].sum(), 1e-9)), 4),
+           "dominant_kernel_gbs": round(kgbs, 2), "dominant_kernel_frac": round(kgbs / peak, 4),
+           "whole_step_gbs": round(wgbs, 2), "whole_step_frac": round(wgbs / peak, 4),
+           "peak_gbs": peak, "peak_kind": f"{peak_kind} copy bandwidth",
+           "kernel_ms_serial": {SLOT_NAMES[i]: round(float(slot_ms[i]), 3)
+                                for i in range(NSLOTS) if slot_ms[i] > 0}}
+    if lstats is not None:
+        out["learned_stats"] = lstats
+    if note:
+        out["note"] = note
+    return out
+
+
+def configs_eval():
+    """One line per workload configuration besides the main one (the
+    batched leg covers the Galerkin batch): the 5-point Laplacian 64x64, the
+    27-point stencil 128^3 with the default and the autotuned bins, and the
+    held-out R-MAT n=2^21, degree 32, whole, in row slabs, plain and learned."""
+    import torch
+
+    import paper_2206_07244_gb300 as ops
+    from paper_2206_07244_gb300 import autotune, learned
+    lines = []
+    L = W.laplacian_2d(64)
+    lines.append(config_line("5-point Laplacian 64x64 (n=4096)", L, [(0, L.rows)], warm=3,
+                             note="latency-bound: 100,104 products; the fraction is reported, not meaningful"))
+    S = W.stencil27(128, seed=3)
+    lines.append(config_line("27-point stencil 128^3, default bins", S, [(0, S.rows)], warm=3))
+    dS = ops.CSR.from_workload(S)
+    best, hist = autotune.tune(dS, dS, reps=2)
+    del dS
+    torch.cuda.empty_cache()
+    tuned = config_line("27-point stencil 128^3, autotuned bins", S, [(0, S.rows)], cfg=best, warm=3)
+    tuned["tuned_config"] = best
+    tuned["trials"] = len(hist)
+    tuned["tuned_over_default"] = round(lines[-1]["ms"] / tuned["ms"], 4)
+    lines.append(tuned)
+    del S
+    R = W.rmat(21, 32, seed=2021)
+    slabs = slabs_by_products(R, 1.5e9)
+    man = json.load(open(learned.MANIFEST))
+    theta = np.load(learned.WEIGHTS)
+    plain = config_line("held-out R-MAT n=2^21, degree 32, seed 2021, whole matrix, plain", R, slabs, warm=1)
+    lines.append(plain)
+    lrn = config_line("held-out R-MAT n=2^21, degree 32, seed 2021, whole matrix, learned sizing", R, slabs,
+                      learned_theta=theta, margin=man["margin"], warm=3)
+    lrn["learned_over_plain"] = round(plain["ms"] / lrn["ms"], 4)
+    # the learned path does not count products; the multiply is the same
+    lrn["nprod"] = plain["nprod"]
+    lrn["gflops"] = round(2.0 * plain["nprod"] / (lrn["ms"] / 1e3) / 1e9, 3)
+    lines.append(lrn)
+    return lines
+
+
 def pick_slab(A, budget_entries):
     """A contiguous row slab of A*A, starting at row A.rows/2, whose C has at
     most budget_entries entries (sized with the library's symbolic phase)."""
@@ -471,14 +665,18 @@ def main():
     ap.add_argument("--window-lists", type=int, default=None,
                     help="set the numeric bitmap kernel's window_lists option on top of the "
                          "configuration in use (0 = whole-row pass 2)")
-    ap.add_argument("--legs", default="all", choices=["all", "none", "learned", "batched", "ablation"],
+    ap.add_argument("--legs", default="all",
+                    choices=["all", "none", "learned", "batched", "ablation", "peaks", "configs"],
                     help="extra comparisons after the main line: learned sizing vs plain "
-                         "(trained weights), 512 Galerkin products plain vs batched, and "
-                         "single- vs multi-access hash probes")
+                         "(trained weights), 512 Galerkin products plain vs batched, "
+                         "single- vs multi-access hash probes, the operation-rate probes, and "
+                         "one line per other workload configuration")
     args = ap.parse_args()
     args.learned = args.legs in ("all", "learned")
     args.batched = args.legs in ("all", "batched")
     args.ablation = args.legs in ("all", "ablation")
+    args.peaks = args.legs in ("all", "peaks")
+    args.configs = args.legs in ("all", "configs")
     if args.warmup < 3 and args.impl == "ours" and not os.environ.get("BENCH_ALLOW_SHORT"):
         args.warmup = 3
     if args.impl == "reference":
@@ -606,16 +804,31 @@ def main():
     avg_ms = kms[k] / launches
     peak, peak_kind = peaks()
     achieved = algo / (avg_ms / 1e3) / 1e9
-    # measured DRAM traffic of this launch where a capture of the same kernel,
-    # workload and configuration exists (the default one, whole matrix, 1 GPU)
+    # intermediate products of the dominant kernel's launch (the rows of its
+    # bin), from one more step's row sizes: the units the operation-rate
+    # ceilings count
+    is_num_bitmap = 16 <= k < 32 and k - 16 == len(h.get_config()["num_kernel"]) - 1
+    kernel_products = None
+    if is_num_bitmap:
+        C = step()
+        nnz_row = np.diff(C.rpt.cpu().numpy())
+        del C
+        cut = h.get_config()["num_range"][-2] if len(h.get_config()["num_range"]) > 1 else -1
+        cs = np.concatenate([[0], np.cumsum(np.diff(rpt64)[A.col])])
+        row_np = cs[rpt64[1:]] - cs[rpt64[:-1]]
+        kernel_products = int(row_np[r0:r1][nnz_row > cut].sum())
+    # DRAM traffic of this launch, scaled from a windowed capture of the same
+    # kernel sources, workload and configuration (default, whole matrix, 1 GPU)
     traffic = traffic_src = None
-    cfg_now = h.get_config()
-    if k < 32 and k >= 16 and k - 16 == len(cfg_now["num_kernel"]) - 1 and ws == 1 \
-            and args.rows is None and not args.window_lists and args.config is None:
-        traffic = TRAFFIC.get((args.workload, "num_bitmap_kernel"))
-        if traffic is not None:
-            traffic_src = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch " \
-                          "(profiles/num_bitmap_kernel_rmat20.md)"
+    tw = TRAFFIC_WINDOWED.get((args.workload, "num_bitmap_kernel"))
+    if is_num_bitmap and tw and kernel_products and ws == 1 and args.rows is None \
+            and not args.window_lists and args.config is None and tw["sources_sha"] == kernel_sources_sha():
+        scale = kernel_products / tw["window_products"]
+        traffic = int(tw["dram_bytes"] * scale)
+        traffic_src = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of the launch for rows "
+                       f"{tw['rows']} ({tw['dram_bytes']} bytes, {tw['window_products']} products), "
+                       f"scaled by products x{scale:.2f}")
+    rates = op_rates(lib) if args.peaks and rank == 0 else None
     roofline = {"bound": "hbm", "kernel": SLOT_NAMES[k], "achieved": round(achieved, 2),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "traffic_source": traffic_src,
@@ -624,6 +837,17 @@ def main():
                 "algorithmic_bytes_per_launch": int(algo), "avg_launch_ms": round(avg_ms, 4),
                 "serial_launch_ms": round(sms_[k] / max(sln[k], 1), 4),
                 "bytes_model": algo_desc}
+    if kernel_products:
+        # beside the memory roofline: every product costs one float64
+        # multiply(-add) and one scattered float64 accumulation
+        prate = kernel_products / (avg_ms / 1e3) / 1e9
+        roofline["products_per_launch"] = kernel_products
+        roofline["products_gops"] = round(prate, 2)
+        if rates:
+            roofline["atomic_frac"] = round(prate / rates["l2_red_scattered_gops"], 4)
+            roofline["atomic_peak_gops"] = rates["l2_red_scattered_gops"]
+            roofline["fp64_frac"] = round(prate / rates["fp64_fma_gops"], 4)
+            roofline["fp64_peak_gops"] = rates["fp64_fma_gops"]
     whole = {"bytes_per_step": int(total_bytes),
              "achieved_gbs": round(total_bytes / (ms / args.steps / 1e3) / 1e9, 2),
              "frac": round(total_bytes / (ms / args.steps / 1e3) / 1e9 / peak, 4)}
@@ -688,7 +912,10 @@ def main():
     if not args.no_cpu_baseline and rank == 0 and ws == 1:
         cpu = cpu_baseline(A)
 
-    learned_legs = batched = ablation = None
+    learned_legs = batched = ablation = configs = None
+    if args.configs and rank == 0:
+        configs = configs_eval()
+        torch.cuda.empty_cache()
     if args.ablation and rank == 0:
         ablation = hash_ablation_eval()
         torch.cuda.empty_cache()
@@ -696,11 +923,9 @@ def main():
         batched = batched_eval()
         torch.cuda.empty_cache()
     if args.learned and rank == 0:
+        # (the held-out R-MAT n=2^21 is measured whole, in row slabs, by the
+        # configs leg)
         learned_legs = []
-        R = W.rmat(21, 32, seed=2021)
-        r0, r1 = pick_slab(R, 2_000_000_000)
-        learned_legs.append(learned_eval("held-out R-MAT n=2^21, degree 32, seed 2021", R, r0, r1))
-        del R
         S = W.stencil27(128, seed=3)
         learned_legs.append(learned_eval("27-point stencil 128^3", S, 0, S.rows))
         del S
@@ -724,6 +949,7 @@ def main():
                 "stage_ms_live": breakdown, "kernel_ms_serial": serial,
                 "bins": bins, "autotune": tuned, "numeric_values": rerun,
                 "learned": learned_legs, "batched": batched, "hash_access": ablation,
+                "op_rates": rates, "configs": configs,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)

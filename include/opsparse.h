@@ -109,7 +109,10 @@ typedef void (*spgemm_free_fn)(void *ptr, void *stream, void *ctx);
  * computed. All forms give the same C.
  *   0 (the default): one block per row with a column bitmap and its ranks
  *     in shared memory, one window over the whole column space when it fits;
- *     the values are summed in C.val by float64 L2 reductions.
+ *     the values are summed in C.val by float64 L2 reductions. When B has
+ *     more columns than one bitmap holds, the row is covered in several
+ *     windows; with every row of B sorted by column (and at most 2^22
+ *     columns) each window then walks only the runs of B rows inside it.
  *   1: the same, but when every row of B is sorted by column and B has at
  *     most 2^22 columns a row is covered in column windows of about half an
  *     SM's shared memory (two blocks per SM), each window walking only the

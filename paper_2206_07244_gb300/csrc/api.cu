@@ -17,6 +17,7 @@
 //               freed between launches (Sec. 5.5).
 #include <algorithm>
 #include <climits>
+#include <mutex>
 #include <vector>
 #include <cstdio>
 #include <cstring>
@@ -133,6 +134,7 @@ struct spgemm_handle {
     bool win_used = false;        // the last numeric call ran the column windows
     // whole-row bitmap kernel walked by half-width column windows (sorted B)
     bool split_on = false;        // planned by the symbolic call
+    bool split_idx = false;       // the symbolic call built the cell index of B
     bool split_keep = false;      // the last numeric call used it (index kept)
     int split_cs = 0, split_ncells = 0;
     // per-kernel CUDA-event timing (off unless requested)
@@ -313,13 +315,9 @@ void default_config(spgemm_config &c) {
     std::memset(&c, 0, sizeof(c));
     // Symbolic: every table at least 1.2x the largest n_prod of its bin
     // (Sec. 5.7, the paper's choice "Sym_1.2x"); the bitmap takes the rest.
-    const int ns = sym_kernel_count();
-    c.sym_nbins = ns;
-    for (int j = 0; j < ns; ++j) {
-        c.sym_kernel[j] = j;
-        const KernelDesc &d = sym_kernel(j);
-        c.sym_range[j] = d.bitmap ? -1 : static_cast<int64_t>(d.table * 5 / 6);
-    }
+    long long sr[kMaxBins];
+    c.sym_nbins = default_sym_bins(sr, c.sym_kernel);
+    for (int j = 0; j < c.sym_nbins; ++j) c.sym_range[j] = sr[j];
     // Numeric: every table at least 2x the largest n_nz of its bin (Sec. 5.7,
     // "Num_2x").
     const int nn = num_kernel_count();
@@ -416,15 +414,19 @@ bool win_setup(spgemm_handle *h, int64_t ncols) {
     return true;
 }
 
-// Whole-row numeric bitmap kernel by column windows: every row of the
-// last numeric bin is covered in windows of about half the shared memory of
-// an SM, so two blocks run per SM (one block's bitmap and C.col phases
-// overlap the other's float64 reductions), and with rows of B sorted each
-// window walks only the runs of B rows inside it (cell index of the long B
-// rows). Needs at most kWinMaxCells cells of 2^cs >= 2^12 columns.
+// Whole-row numeric bitmap kernel by column windows with rows of B sorted:
+// each window walks only the runs of B rows inside it (cell index of the
+// long B rows), instead of every product of the row once per window. Form 0
+// uses it when one bitmap cannot hold every column; form 1 always, with
+// windows of about half an SM's shared memory so two blocks run per SM (one
+// block's bitmap and C.col phases overlap the other's float64 reductions).
+// Needs at most kWinMaxCells cells of 2^cs >= 2^12 columns.
 bool split_setup(spgemm_handle *h, int64_t ncols) {
     const spgemm_config &c = h->cfg;
-    if (c.bitmap_path != 1 || ncols <= 0 || ncols > (int64_t{1} << kWinMaxColsLog2)) return false;
+    if (c.bitmap_path > 1 || ncols <= 0 || ncols > (int64_t{1} << kWinMaxColsLog2)) return false;
+    // form 0 needs windows only when one bitmap cannot hold every column
+    const int64_t full = (h->smem_dyn_max - static_cast<int64_t>(num_bitmap_head_bytes(false))) / 12 * 64;
+    if (c.bitmap_path == 0 && ncols <= full) return false;
     if (c.window_lists > 0 || !num_kernel(c.num_kernel[c.num_nbins - 1]).bitmap) return false;
     int lg = 0;
     while ((int64_t{1} << lg) < ncols) ++lg;
@@ -455,6 +457,7 @@ void win_release(spgemm_handle *h) {
     h->wbidx = nullptr;
     h->wctr = nullptr;
     h->wkeep = false;
+    h->split_idx = false;
 }
 
 // L2 spill slots of the window kernel: one accumulator's worth per block,
@@ -467,6 +470,30 @@ int ensure_spill(spgemm_handle *h, long long stride) {
     h->wspill_bytes = h->wspill ? need : 0;
     if (!h->wspill) return SPGEMM_ERR_OOM;
     return cudaMemsetAsync(h->wspill, 0, need, h->stream) == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
+}
+
+// Cell index of B's long rows (launch_win_bindex), kept in the handle.
+int build_bindex(spgemm_handle *h, const Operands &op, const spgemm_csr_in *B) {
+    const long long min_len = std::max<long long>(32, (h->split_ncells + 1) / 2);
+    const long long cap = B->nnz / min_len + 1;
+    h->wctr = static_cast<unsigned long long *>(dev_alloc(h, 4 * sizeof(unsigned long long)));
+    h->wbslot = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * (size_t)std::max<int64_t>(B->rows, 1)));
+    h->wbidx = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * (size_t)cap * (size_t)(h->split_ncells + 1)));
+    if (!h->wctr || !h->wbslot || !h->wbidx) {
+        win_release(h);
+        return SPGEMM_ERR_OOM;
+    }
+    WinPlan ip;
+    ip.cs = h->split_cs;
+    ip.ncells = h->split_ncells;
+    if (cudaMemsetAsync(h->wctr, 0, 4 * sizeof(unsigned long long), h->stream) != cudaSuccess ||
+        launch_win_bindex(op, B->rows, ip, min_len, h->wbslot, h->wbidx, cap, h->wctr + 2, h->stream) !=
+            cudaSuccess) {
+        win_release(h);
+        return SPGEMM_ERR_CUDA;
+    }
+    h->split_idx = true;
+    return SPGEMM_OK;
 }
 
 // What the numeric phase needs to run the last bin by column windows.
@@ -569,6 +596,16 @@ int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *s
             if (phase == 0) {
                 const int64_t budget = h->smem_dyn_max - static_cast<int64_t>(sizeof(WalkScratch));
                 int64_t words = std::min<int64_t>((op.ncols + 31) / 32, budget / 4);
+                if (h->split_idx) {
+                    // several passes over the columns: each walks only its runs
+                    w.bslot = h->wbslot;
+                    w.bidx = h->wbidx;
+                    w.cs = h->split_cs;
+                    w.ncells = h->split_ncells;
+                    w.bflags = &d_counters(h, 1)->flags;
+                    const int64_t cwords = int64_t{1} << (h->split_cs - 5);
+                    if (words < (op.ncols + 31) / 32) words = std::max<int64_t>(cwords, (words / cwords) * cwords);
+                }
                 if (win && win->on && h->wcells) {
                     // per-cell counts: a pass covers whole cells
                     const int64_t cwords = int64_t{1} << (h->wplan.cs - 5);
@@ -591,14 +628,16 @@ int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *s
                 int64_t budget = h->smem_dyn_max - static_cast<int64_t>(num_bitmap_head_bytes(r));
                 const bool split = !r && win && win->split;
                 if (split) {
-                    // half an SM's shared memory per block (two blocks per SM),
-                    // windows of whole cells
-                    budget = std::min<int64_t>(budget, (228 * 1024 - 2 * 1024) / 2 - 512 -
-                                                           static_cast<int64_t>(num_bitmap_head_bytes(false)));
                     w.bslot = win->bslot;
                     w.bidx = win->bidx;
                     w.cs = win->cs;
                     w.ncells = win->ncells;
+                }
+                if (split && h->cfg.bitmap_path == 1) {
+                    // half an SM's shared memory per block (two blocks per SM),
+                    // windows of whole cells
+                    budget = std::min<int64_t>(budget, (228 * 1024 - 2 * 1024) / 2 - 512 -
+                                                           static_cast<int64_t>(num_bitmap_head_bytes(false)));
                 }
                 int64_t words = std::min<int64_t>((op.ncols + 63) / 64, budget / 12);
                 if (split && words < (op.ncols + 63) / 64) {
@@ -762,7 +801,16 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
         w.unroll = h->cfg.bitmap_unroll;
         w.err = d_err(h);
         const int64_t budget = h->smem_dyn_max - static_cast<int64_t>(sizeof(WalkScratch));
-        const int64_t words = std::min<int64_t>((op.ncols + 31) / 32, budget / 4);
+        int64_t words = std::min<int64_t>((op.ncols + 31) / 32, budget / 4);
+        if (h->split_idx) {   // several column passes: each walks only its runs
+            w.bslot = h->wbslot;
+            w.bidx = h->wbidx;
+            w.cs = h->split_cs;
+            w.ncells = h->split_ncells;
+            w.bflags = &d_counters(h, 1)->flags;
+            const int64_t cwords = int64_t{1} << (h->split_cs - 5);
+            if (words < (op.ncols + 31) / 32) words = std::max<int64_t>(cwords, (words / cwords) * cwords);
+        }
         time_begin(h, kSlotSymBin + 15, s);
         CK(launch_sym(sym_kernel_count() - 1, op, w, static_cast<size_t>(std::max<int64_t>(words, 1)) * 4, s));
         time_end(h, kSlotSymBin + 15, s);
@@ -778,6 +826,7 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
         reinterpret_cast<unsigned char *>(h->h_cnt) + 2 * sizeof(Counters) + 64);
     CK(cudaMemcpyAsync(h_fb, L.fb, sizeof(unsigned long long) * kFbCounters, cudaMemcpyDeviceToHost, s));
     if ((rc = read_counters(h))) return rc;
+    h->b_unsorted = (h->h_cnt[1].flags & 1ull) != 0;
     *nnz_out = static_cast<int64_t>(h->h_cnt[1].total);
     h->lstats[0] = 0;
     for (int j = 0; j < last; ++j) h->lstats[0] += h->lsize[j];
@@ -850,7 +899,15 @@ int numeric_learned(spgemm_handle *h, const Operands &op, int64_t *crpt, int32_t
         w.unroll = h->cfg.bitmap_unroll;
         w.err = d_err(h);
         const int64_t budget = h->smem_dyn_max - static_cast<int64_t>(num_bitmap_head_bytes(false));
-        const int64_t words = std::min<int64_t>((op.ncols + 63) / 64, budget / 12);
+        int64_t words = std::min<int64_t>((op.ncols + 63) / 64, budget / 12);
+        if (h->split_idx && !h->b_unsorted) {   // several column windows: each walks only its runs
+            w.bslot = h->wbslot;
+            w.bidx = h->wbidx;
+            w.cs = h->split_cs;
+            w.ncells = h->split_ncells;
+            const int64_t cwords = int64_t{1} << (h->split_cs - 6);
+            if (words < (op.ncols + 63) / 64) words = std::max<int64_t>(cwords, (words / cwords) * cwords);
+        }
         time_begin(h, kSlotNumBin + 15, s);
         CK(launch_num(num_kernel_count() - 1, op, w, static_cast<size_t>(std::max<int64_t>(words, 1)) * 12, s));
         time_end(h, kSlotNumBin + 15, s);
@@ -911,8 +968,7 @@ int spgemm_create(spgemm_handle **out, const spgemm_config *cfg, spgemm_alloc_fn
         cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
         h->smem_dyn_max = optin - 1024;  // room for the kernels' static shared arrays
-        if (sym_prepare(h->smem_dyn_max) != cudaSuccess || num_prepare(h->smem_dyn_max) != cudaSuccess ||
-            win_prepare(h->smem_dyn_max) != cudaSuccess) {
+        if (prepare_device(h->device, h->smem_dyn_max) != cudaSuccess) {
             rc = SPGEMM_ERR_CUDA;
             break;
         }
@@ -1001,8 +1057,9 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     if (h->cfg_auto) auto_cut(h->cfg, B->cols);
     win_release(h);
     h->wp_on = h->mode == SPGEMM_MODE_PLAIN && win_setup(h, B->cols);
-    h->split_on = h->mode == SPGEMM_MODE_PLAIN && split_setup(h, B->cols);
+    h->split_on = split_setup(h, B->cols);
     h->split_keep = false;
+    h->split_idx = false;
     h->nwin = 0;
     h->nwin_col = 0;
     h->win_used = false;
@@ -1018,6 +1075,15 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
         note(cudaMemsetAsync(crpt, 0, sizeof(int64_t) * (size_t)(mw + 1), h->stream)) != cudaSuccess)
         return fail(SPGEMM_ERR_CUDA);
     const Operands op = make_operands(A, B, row_begin, mw);
+    // cell index of B's long rows for kernels that cover rows in several
+    // column windows (built here, used by both phases; the symbolic kernel
+    // checks on the device that B is sorted)
+    if (h->split_on) {
+        if (note(launch_sorted_check(op, B->rows, B->nnz, d_counters(h, 1), h->sm_count * 4, h->stream)) !=
+            cudaSuccess)
+            return fail(SPGEMM_ERR_CUDA);
+        if ((rc = build_bindex(h, op, B))) return fail(rc);
+    }
     if (h->mode == SPGEMM_MODE_LEARNED) {
         // the one-phase kernels multiply during this call: they read values
         if ((A->nnz > 0 && !A->val) || (B->nnz > 0 && !B->val)) return fail(SPGEMM_ERR_INVALID);
@@ -1047,7 +1113,7 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     if (note(launch_nprod(op, crpt, h->sm_count * 8, h->stream)) != cudaSuccess) return fail(SPGEMM_ERR_CUDA);
     time_end(h, kSlotNprod, h->stream);
     h->rplan = run_plan(h->cfg, h->smem_dyn_max, B->cols);
-    if ((h->rplan.lists > 0 || h->wp_on || h->split_on) &&
+    if ((h->rplan.lists > 0 || h->wp_on) && !h->split_on &&
         note(launch_sorted_check(op, B->rows, B->nnz, d_counters(h, 1), h->sm_count * 4, h->stream)) !=
             cudaSuccess)
         return fail(SPGEMM_ERR_CUDA);
@@ -1242,31 +1308,13 @@ int spgemm_numeric(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_in
         wc.ww.spill = h->wspill;
         rp = RunPlan{};
     }
-    // whole-row bitmap kernel by column windows: cell index of B's long rows
-    if (!wc.on && h->split_on && !h->b_unsorted && h->num_size[last] > 0 && rp.lists == 0 &&
+    // whole-row bitmap kernel by column windows over the cell index that the
+    // symbolic call built
+    if (!wc.on && h->split_idx && !h->b_unsorted && h->num_size[last] > 0 && rp.lists == 0 &&
         num_kernel(h->cfg.num_kernel[last]).bitmap) {
-        win_release(h);
         wc.split = true;
         wc.cs = h->split_cs;
         wc.ncells = h->split_ncells;
-        wc.min_len = std::max<long long>(32, (h->split_ncells + 1) / 2);
-        wc.bcap = B->nnz / wc.min_len + 1;
-        h->wctr = static_cast<unsigned long long *>(dev_alloc(h, 4 * sizeof(unsigned long long)));
-        h->wbslot = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * (size_t)std::max<int64_t>(B->rows, 1)));
-        h->wbidx = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * (size_t)wc.bcap * (size_t)(wc.ncells + 1)));
-        if (!h->wctr || !h->wbslot || !h->wbidx) {
-            win_release(h);
-            return fail(SPGEMM_ERR_OOM);
-        }
-        WinPlan ip;
-        ip.cs = wc.cs;
-        ip.ncells = wc.ncells;
-        if (note(cudaMemsetAsync(h->wctr, 0, 4 * sizeof(unsigned long long), h->stream)) != cudaSuccess ||
-            note(launch_win_bindex(op, B->rows, ip, wc.min_len, h->wbslot, h->wbidx, wc.bcap, h->wctr + 2,
-                                   h->stream)) != cudaSuccess) {
-            win_release(h);
-            return fail(SPGEMM_ERR_CUDA);
-        }
         wc.bslot = h->wbslot;
         wc.bidx = h->wbidx;
     }
@@ -2030,3 +2078,21 @@ int spgemm_batch_destroy(spgemm_batch *b) {
 }
 
 }  // extern "C"
+
+namespace ops {
+
+cudaError_t prepare_device(int dev, int smem_dyn_max) {
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static bool done[kMaxDev] = {};
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return cudaSuccess;
+    cudaError_t e = sym_prepare(smem_dyn_max);
+    if (e == cudaSuccess) e = num_prepare(smem_dyn_max);
+    if (e == cudaSuccess) e = win_prepare(smem_dyn_max);
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
+}  // namespace ops

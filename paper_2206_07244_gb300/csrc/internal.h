@@ -74,6 +74,9 @@ struct BinWork {
     // sorted: cell index of the long B rows, so each window walks only its runs
     const int32_t *bslot;
     const int32_t *bidx;
+    // symbolic bitmap kernel: bit 0 set = some row of B is not sorted (the
+    // runs are then not used); nullptr = B known sorted
+    const unsigned long long *bflags;
 };
 
 struct Ranges {
@@ -135,6 +138,12 @@ const KernelDesc &sym_kernel(int id);
 const KernelDesc &num_kernel(int id);
 cudaError_t sym_prepare(int device_smem_optin);
 cudaError_t num_prepare(int device_smem_optin);
+// Default symbolic bin ranges and kernels (returns the bin count).
+int default_sym_bins(long long *range, int32_t *kernel);
+// Kernel attributes of every kernel on device `dev` (the current device),
+// once per device; serialised by a lock, so handles and the
+// allocation-free entry point may be set up from several host threads.
+cudaError_t prepare_device(int dev, int smem_dyn_max);
 cudaError_t launch_sym(int id, const Operands &op, const BinWork &w, size_t smem_bitmap,
                        cudaStream_t s);
 cudaError_t launch_num(int id, const Operands &op, const BinWork &w, size_t smem_bitmap,

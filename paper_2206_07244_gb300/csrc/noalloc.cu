@@ -49,11 +49,13 @@ int setup_device(int dev, unsigned char **scratch, int *smem_dyn_max) {
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return SPGEMM_ERR_CUDA;
     *smem_dyn_max = optin - 1024;
+    // kernel attributes: the same once-per-device step as spgemm_create,
+    // under its own lock
+    if (prepare_device(dev, *smem_dyn_max) != cudaSuccess) return SPGEMM_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_prepared[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return SPGEMM_ERR_CUDA;
-        if (sym_prepare(*smem_dyn_max) != cudaSuccess) return SPGEMM_ERR_CUDA;
         g_scratch_addr[dev] = static_cast<unsigned char *>(p);
         g_prepared[dev] = true;
     }
@@ -104,13 +106,8 @@ extern "C" int spgemm_rowptr_noalloc(const spgemm_csr_in *A, const spgemm_csr_in
     // default symbolic bins: every hash table at least 1.2x its bin's
     // largest n_prod, the bitmap kernel for the rest
     Ranges rs{};
-    rs.nb = sym_kernel_count();
     int32_t kid[kMaxBins];
-    for (int j = 0; j < rs.nb; ++j) {
-        kid[j] = j;
-        const KernelDesc &d = sym_kernel(j);
-        rs.r[j] = d.bitmap ? -1 : d.table * 5 / 6;
-    }
+    rs.nb = default_sym_bins(rs.r, kid);
     if (launch_bin_pass1(crpt, mw, rs, op, cnt, nullptr, s) != cudaSuccess) return SPGEMM_ERR_CUDA;
     Counters host[2];
     int herr = 0;

@@ -102,7 +102,10 @@ sym_hash_kernel(Operands op, BinWork w) {
     if (valid && lg == 0) w.crpt[row] = cnt;
 }
 
-template <int BLOCK, int ITERS>
+// RUNS: several column passes over sorted B; each pass walks only the runs
+// of B rows inside it (w.bslot / w.bidx), unless the device flag says some
+// row of B is unsorted.
+template <int BLOCK, int ITERS, bool RUNS = false>
 __global__ void __launch_bounds__(BLOCK, BLOCK == 1024 ? 1 : 1536 / BLOCK)
 sym_bitmap_kernel(Operands op, BinWork w, int words) {
     constexpr int kBmBlock = BLOCK;
@@ -129,10 +132,16 @@ sym_bitmap_kernel(Operands op, BinWork w, int words) {
         __syncthreads();
         const int c0i = static_cast<int>(c0);
         const unsigned span32 = static_cast<unsigned>(span);
-        block_row_walk<kBmBlock, false, ITERS>(op, p0, p1, S, sc, [&](int key, double, double) {
+        RunSel rsel{w.bslot, w.bidx, w.cs, w.ncells, c0i,
+                    static_cast<int>(c0 + span < op.ncols ? c0 + span : op.ncols)};
+        if (RUNS && w.bflags && (*w.bflags & 1ull)) {   // unsorted B: whole rows, filtered
+            rsel.c0 = 0;
+            rsel.c1 = INT_MAX;
+        }
+        block_row_walk<kBmBlock, false, ITERS, 0, RUNS>(op, p0, p1, S, sc, [&](int key, double, double) {
             const unsigned rel = static_cast<unsigned>(key - c0i);   // one compare covers both ends
             if (rel < span32) atomicOr(bm + (rel >> 5), 1u << (rel & 31));
-        });
+        }, &rsel);
         if (cells) {
             // one warp per cell: its words' bits, summed over the warp
             const int cwords = 1 << (w.cs - 5);
@@ -202,6 +211,18 @@ const KernelDesc &sym_kernel(int id) {
     return id < kSymHash ? g_sym[id].d : g_sym_bitmap;
 }
 
+// Default symbolic bins: every hash table at least 1.2x the largest n_prod
+// of its bin (Sec. 5.7, the paper's "Sym_1.2x"), the bitmap kernel for the
+// rest. The one rule both the handle's default configuration and the
+// allocation-free entry point use.
+int default_sym_bins(long long *range, int32_t *kernel) {
+    for (int j = 0; j < kSymHash + 1; ++j) {
+        kernel[j] = j;
+        range[j] = j < kSymHash ? g_sym[j].d.table * 5 / 6 : -1;
+    }
+    return kSymHash + 1;
+}
+
 cudaError_t sym_prepare(int smem_optin) {
     // Opt in for every kernel: the 48 KB default covers static plus dynamic
     // shared memory, so a table of exactly 48 KB already needs it.
@@ -221,7 +242,8 @@ cudaError_t sym_prepare(int smem_optin) {
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return cudaFuncSetAttribute(reinterpret_cast<const void *>(&sym_bitmap_kernel<1024, 4, true>),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
 }
 
 // Same launch-shape rule as the numeric bitmap kernel: about 2048 threads
@@ -250,6 +272,10 @@ cudaError_t launch_sym(int id, const Operands &op, const BinWork &w, size_t smem
     } else {
         const int words = static_cast<int>(smem_bitmap / 4);
         const size_t smem = smem_bitmap + sizeof(WalkScratch);
+        if (w.bidx && static_cast<int64_t>(words) * 32 < op.ncols) {
+            sym_bitmap_kernel<1024, 4, true><<<static_cast<unsigned>(w.cnt), 1024, smem, s>>>(op, w, words);
+            return cudaGetLastError();
+        }
         const auto &v = g_sym_bm[pick_sym_bitmap_variant(smem, w.unroll)];
         v.fn<<<static_cast<unsigned>(w.cnt), v.block, smem, s>>>(op, w, words);
     }

@@ -265,3 +265,37 @@ def test_split_numeric_values_rerun():
             C2 = h.numeric_values(dA, dev(B2), C)
             h.status()
             check(A, B2, C2.numpy())
+
+
+def test_default_form_walks_runs_when_columns_exceed_one_bitmap():
+    # 3M columns do not fit one bitmap: the default form covers each row in
+    # windows that walk only their runs (sorted B)
+    A, B = wide_dense(10, 40, 3_000_000, 9000, 3_000_000, seed=27)
+    got, st = run(A, B, bitmap_bin_only(path=0))
+    assert st["split"]
+    check(A, B, got)
+
+
+def test_default_form_unsorted_wide_b():
+    # the symbolic bitmap kernel's runs are switched off on the device when
+    # some row of B is unsorted; the numeric kernel walks whole rows
+    A, B = wide_dense(8, 30, 3_000_000, 9000, 3_000_000, seed=28)
+    col = B.col.copy()
+    col[B.rpt[2]:B.rpt[3]] = col[B.rpt[2]:B.rpt[3]][::-1]
+    B2 = W.Csr(B.rows, B.cols, B.rpt, col, B.val.copy())
+    got, st = run(A, B2)
+    assert not st["split"]
+    check(A, B2, got)
+
+
+def test_learned_mode_wide_b_exact_rows_walk_runs():
+    from paper_2206_07244_gb300 import learned
+    A, B = wide_dense(10, 36, 3_000_000, 9000, 3_000_000, seed=29)
+    theta = np.load(learned.WEIGHTS)
+    with ops.Handle() as h:
+        h.set_predictor(theta, 0.0)
+        h.set_mode("learned")
+        dA, dB = dev(A), dev(B)
+        C = h.multiply(dA, dB)
+        h.status()
+        check(A, B, C.numpy())

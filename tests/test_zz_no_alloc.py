@@ -4,15 +4,19 @@ spgemm_rowptr_noalloc serves callers that cannot call cudaMalloc at run
 time (for example, when another framework's allocator owns all device
 memory): it computes C's row pointer with scratch held in a fixed array
 inside the library. Here its output is compared, through the C ABI, with the
-row pointer that spgemm_symbolic + spgemm_numeric produce, on two calls in a
-row, so that contents the array keeps from one call cannot leak into the
-next. This file is collected last on purpose."""
+row pointer that spgemm_symbolic + spgemm_numeric produce and with the CPU
+oracle's row sizes and exclusive scan, on two calls in a row, so that
+contents the array keeps from one call cannot leak into the next; and at
+the edges: an A with no rows, an A with exactly the largest accepted number
+of rows, and a B wide enough that the bitmap kernel takes two passes. This
+file is collected last on purpose."""
 
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -83,6 +87,56 @@ def test_noalloc_rowptr_matches_regular_entry_point(case):
         assert rc == 0
         assert np.array_equal(got, want)
         assert nnz == want[-1]
+
+
+def _rowptr_oracle(A, B):
+    return oracle.exclusive_scan(oracle.symbolic(A, B))
+
+
+@pytest.mark.parametrize("case", ["rmat", "dense_row"])
+def test_noalloc_rowptr_matches_oracle(case):
+    A, B = (W.rmat(13, 8, seed=9),) * 2 if case == "rmat" else _dense_row_case()
+    want = _rowptr_oracle(A, B)
+    for _ in range(2):
+        rc, got, nnz = _rowptr_noalloc(A, B)
+        assert rc == 0
+        assert np.array_equal(got, want)
+        assert nnz == want[-1]
+
+
+def test_noalloc_empty_a():
+    A = W.Csr(0, 16, np.zeros(1, dtype=np.int32), np.zeros(0, dtype=np.int32), np.zeros(0))
+    B = W.rmat(4, 4, seed=1)
+    for _ in range(2):
+        rc, got, nnz = _rowptr_noalloc(A, B)
+        assert rc == 0 and got.tolist() == [0] and nnz == 0
+
+
+def test_noalloc_largest_accepted_size():
+    # exactly SPGEMM_NOALLOC_MAX_ROWS rows (fills the bins and tile-sum
+    # regions of the fixed array) with a few non-zeros
+    n = 1 << 20
+    rng = np.random.default_rng(41)
+    rows = np.sort(rng.choice(n, 3000, replace=False))
+    A = W._from_coo(n, 64, rows, rng.integers(0, 64, rows.size), np.ones(rows.size))
+    B = W.random_csr(64, 5000, 0.05, seed=42)
+    want = _rowptr_oracle(A, B)
+    rc, got, nnz = _rowptr_noalloc(A, B)
+    assert rc == 0 and np.array_equal(got, want) and nnz == want[-1]
+
+
+def test_noalloc_columns_past_one_bitmap_pass():
+    # 3M columns: the symbolic bitmap kernel covers them in two passes
+    rng = np.random.default_rng(43)
+    K, N = 40, 3_000_000
+    br = np.repeat(np.arange(K), 6000)
+    bc = np.concatenate([np.sort(rng.choice(N, 6000, replace=False)) for _ in range(K)])
+    B = W._from_coo(K, N, br, bc, np.ones(bc.size))
+    A = W._from_coo(4, K, np.repeat(np.arange(4), K), np.tile(np.arange(K), 4), np.ones(4 * K))
+    want = _rowptr_oracle(A, B)
+    for _ in range(2):
+        rc, got, nnz = _rowptr_noalloc(A, B)
+        assert rc == 0 and np.array_equal(got, want) and nnz == want[-1]
 
 
 def test_noalloc_rejects_too_many_rows():
