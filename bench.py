@@ -96,17 +96,21 @@ def op_rates(lib):
     from paper_2206_07244_gb300 import _abi
     buf = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
     out = {}
-    for name, op, it in (("fp64_fma_gops", 0, 8192), ("smem_cas_fma_gops", 1, 32768),
-                         ("l2_red_scattered_gops", 5, 32768), ("l2_red_coalesced_gops", 7, 65536),
-                         ("dram_red_scattered_gops", 6, 4096), ("smem_or_u32_gops", 3, 131072)):
+    for name, op, hot, it in (("fp64_fma_gops", 0, 0, 8192), ("smem_cas_fma_gops", 1, 0, 32768),
+                              ("smem_cas_fma_hot1024_gops", 1, 1024, 8192),
+                              ("smem_cas_fma_hot64_gops", 1, 64, 2048),
+                              ("smem_atomicadd_f64_gops", 2, 0, 32768),
+                              ("l2_red_scattered_gops", 5, 0, 32768), ("l2_red_coalesced_gops", 7, 0, 65536),
+                              ("dram_red_scattered_gops", 6, 0, 4096), ("smem_or_u32_gops", 3, 0, 131072),
+                              ("smem_cas_i32_gops", 4, 0, 131072)):
         g = ctypes.c_double()
-        _abi.check(lib.spgemm_probe(op, 0, it, ctypes.c_void_p(buf.data_ptr()), buf.numel(),
+        _abi.check(lib.spgemm_probe(op, hot, it, ctypes.c_void_p(buf.data_ptr()), buf.numel(),
                                     ctypes.byref(g), None), "spgemm_probe")
         out[name] = round(g.value, 2)
     del buf
     torch.cuda.empty_cache()
-    out["what"] = ("one 1024-thread block per SM, uniform random addresses (fma: 8 independent "
-                   "chains per thread); Gop/s")
+    out["what"] = ("one 1024-thread block per SM, uniform random addresses unless hotN (N distinct "
+                   "addresses per block; fma: 8 independent chains per thread); Gop/s")
     return out
 
 
