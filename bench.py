@@ -20,7 +20,9 @@ in HBM when the timed region starts; A (193 MB) is larger than L2 and every
 step writes about 116 GB of C, so nothing stays L2-resident between steps.
 
 Under torchrun (N > 1) each rank computes a contiguous slab of C's rows
-(split by A's non-zeros); value = all products / the slowest rank's time.
+(balanced by the prefix sum of the per-row product counts, B replicated);
+the ranks exchange one int64 each (their entry counts, the offsets of their
+parts of C.rpt); value = all products / the slowest rank's time.
 """
 
 from __future__ import annotations
@@ -130,15 +132,12 @@ def dist_env():
 
 
 def row_slab(A, rank, ws):
-    """Contiguous rows of C for this rank, split evenly by A's non-zeros."""
+    """Contiguous rows of C = A*A for this rank, balanced by the prefix sum
+    of the per-row intermediate products (the library's row sharding)."""
     if ws == 1:
         return 0, A.rows
-    rpt = A.rpt.astype(np.int64)
-    cuts = [0] + [int(np.searchsorted(rpt, rpt[-1] * r // ws)) for r in range(1, ws)] + [A.rows]
-    cuts = [min(max(c, 0), A.rows) for c in cuts]
-    for r in range(1, len(cuts)):
-        cuts[r] = max(cuts[r], cuts[r - 1])
-    return cuts[rank], cuts[rank + 1]
+    from paper_2206_07244_gb300 import shard
+    return shard.slab_bounds(shard.nprod_per_row(A.rpt, A.col, A.rpt), ws)[rank]
 
 
 class ClockSampler:
@@ -772,6 +771,8 @@ def main():
     serial = {SLOT_NAMES[i]: round(sms_[i] / max(sln[i], 1), 3) for i in range(len(sms_)) if sms_[i] > 0}
     ms_max = ms
     nprod_all = nprod_slab
+    nnz_all = nnzC_slab
+    rank_offset = 0
     if dist is not None:
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -779,6 +780,10 @@ def main():
         p = torch.tensor([nprod_slab], dtype=torch.int64, device="cuda")
         dist.all_reduce(p)
         nprod_all = int(p.item())
+        # the one exchange of the sharded product: every rank's entry count,
+        # so that its part of C.rpt gets its global offset
+        from paper_2206_07244_gb300 import shard
+        rank_offset, nnz_all = shard.rpt_offset(nnzC_slab)
     value = 2.0 * nprod_all * args.steps / (ms_max / 1e3) / 1e9
 
     # dominant kernel (longest in the serialised pass) and its roofline,
@@ -944,10 +949,11 @@ def main():
                 "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
                 "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": desc, "rows": A.rows, "nnzA": A.nnz,
-                           "nprod": nprod_all, "nnzC": nnzC_slab if ws == 1 else None,
+                           "nprod": nprod_all, "nnzC": nnz_all,
                            "cache": "inputs larger than L2 (A 193 MB for rmat20; each step "
                                     "writes C, far larger than L2)",
-                           "parallelism": f"row slabs x{ws}" if ws > 1 else "single GPU",
+                           "parallelism": (f"row slabs x{ws}, balanced by n_prod; C.rpt offsets by one "
+                                           "all-gather of per-rank nnz") if ws > 1 else "single GPU",
                            "bin_config": "autotuned" if args.config else "default"},
                 "roofline": roofline, "roofline_whole_step": whole,
                 "stage_ms_live": breakdown, "kernel_ms_serial": serial,
