@@ -71,7 +71,7 @@ def _load():
             lib.oracle_numeric.argtypes = [I64, I64, I64, I64, P, P, P, P, P, P,
                                            P, P, P, P, INT]
             lib.oracle_row_checksums.argtypes = [I64, I64, I64, I64, P, P, P, P,
-                                                 P, P, P, P, P, INT]
+                                                 P, P, P, P, P, P, INT]
             lib.oracle_check_csr.argtypes = [I64, I64, P, P]
             lib.oracle_max_threads.argtypes = []
             for f in (lib.oracle_nprod, lib.oracle_symbolic, lib.oracle_numeric,
@@ -183,7 +183,10 @@ def spgemm_csr(A, B):
 
 def row_checksums(A, B, r0: int = 0, r1: int | None = None, threads: int = 0):
     """Per row of [r0, r1): (count, sum of columns, sum of values in column
-    order)."""
+    order, sum over the row's intermediate products of |a_ik * b_kj|). The
+    last is the scale of the value tolerance (every entry of the row within
+    1e-12 of its own sum of |a*b|, so the row's value sum within 1e-12 of
+    this, up to the rounding of the two row sums)."""
     _check_shapes(A, B)
     M, K, arpt, acol, aval = _csr(A)
     _, N, brpt, bcol, bval = _csr(B)
@@ -192,10 +195,11 @@ def row_checksums(A, B, r0: int = 0, r1: int | None = None, threads: int = 0):
     cnt = np.zeros(n, dtype=np.int64)
     cs = np.zeros(n, dtype=np.int64)
     vs = np.zeros(n, dtype=np.float64)
+    ab = np.zeros(n, dtype=np.float64)
     _rc(_load().oracle_row_checksums(r0, r1, K, N, _p(arpt), _p(acol), _p(aval),
                                      _p(brpt), _p(bcol), _p(bval), _p(cnt),
-                                     _p(cs), _p(vs), threads))
-    return cnt, cs, vs
+                                     _p(cs), _p(vs), _p(ab), threads))
+    return cnt, cs, vs, ab
 
 
 def binning(sizes: np.ndarray, ranges) -> dict:

@@ -30,6 +30,7 @@
  * (-1 out-of-range column, -2 non-monotone row pointer, -3 out of memory).
  */
 #include <stdint.h>
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -198,7 +199,7 @@ int oracle_numeric(int64_t r0, int64_t r1, int64_t K, int64_t N,
 int oracle_row_checksums(int64_t r0, int64_t r1, int64_t K, int64_t N,
                          const int64_t *arpt, const int32_t *acol, const double *aval,
                          const int64_t *brpt, const int32_t *bcol, const double *bval,
-                         int64_t *cnt, int64_t *colsum, double *valsum,
+                         int64_t *cnt, int64_t *colsum, double *valsum, double *abssum,
                          int nthreads)
 {
     int rc = 0;
@@ -217,6 +218,7 @@ int oracle_row_checksums(int64_t r0, int64_t r1, int64_t K, int64_t N,
 #pragma omp for schedule(dynamic, 16)
             for (int64_t i = r0; i < r1; ++i) {
                 int64_t len = 0;
+                double as = 0.0;   /* sum over the row's products of |a*b| */
                 for (int64_t p = arpt[i]; p < arpt[i + 1]; ++p) {
                     int64_t k = acol[p];
                     double a = aval[p];
@@ -224,6 +226,7 @@ int oracle_row_checksums(int64_t r0, int64_t r1, int64_t K, int64_t N,
                         int32_t j = bcol[q];
                         if (mark[j] != i) { mark[j] = i; acc[j] = 0.0; list[len++] = j; }
                         acc[j] = acc[j] + a * bval[q];
+                        as = as + fabs(a * bval[q]);
                     }
                 }
                 qsort(list, (size_t)len, sizeof(int32_t), cmp_i32);
@@ -233,6 +236,7 @@ int oracle_row_checksums(int64_t r0, int64_t r1, int64_t K, int64_t N,
                 cnt[i - r0] = len;
                 colsum[i - r0] = cs;
                 valsum[i - r0] = vs;
+                if (abssum) abssum[i - r0] = as;
             }
         }
         free(mark); free(acc); free(list);

@@ -239,8 +239,8 @@ def test_count_invariants(seed):
 
 def test_row_checksums_agree_with_full_product():
     A = W.rmat(9, 8, seed=4)
-    rpt, col, val, _ = oracle.spgemm(A, A)
-    cnt, cs, vs = oracle.row_checksums(A, A)
+    rpt, col, val, ab = oracle.spgemm(A, A)
+    cnt, cs, vs, rab = oracle.row_checksums(A, A)
     assert np.array_equal(cnt, np.diff(rpt))
     for i in range(A.rows):
         assert cs[i] == int(col[rpt[i]:rpt[i + 1]].astype(np.int64).sum())
@@ -249,8 +249,28 @@ def test_row_checksums_agree_with_full_product():
             acc += x
         assert vs[i] == acc
     # windowed calls see the same rows
-    cnt2, cs2, vs2 = oracle.row_checksums(A, A, 100, 300)
+    cnt2, cs2, vs2, rab2 = oracle.row_checksums(A, A, 100, 300)
     assert np.array_equal(cnt2, cnt[100:300]) and np.array_equal(vs2, vs[100:300])
+    assert np.array_equal(rab2, rab[100:300])
+
+
+def test_row_abs_sums_brute_force():
+    """A row's sum of |a*b| over its intermediate products (the tolerance
+    scale of its entries, Eq. 2's products), against a plain Python loop over
+    A's and B's entries, and against the per-entry sums of the full product."""
+    A = W.rmat(8, 6, seed=11)
+    B = W.random_csr(A.cols, 40, 0.1, seed=12)
+    rpt, col, val, ab = oracle.spgemm(A, B)
+    _, _, _, rab = oracle.row_checksums(A, B)
+    arpt, brpt = A.rpt.astype(np.int64), B.rpt.astype(np.int64)
+    for i in range(A.rows):
+        want = 0.0
+        for p in range(arpt[i], arpt[i + 1]):
+            k, a = int(A.col[p]), float(A.val[p])
+            for q in range(brpt[k], brpt[k + 1]):
+                want += abs(a * float(B.val[q]))
+        assert rab[i] == pytest.approx(want, rel=1e-14, abs=0.0)
+        assert rab[i] == pytest.approx(float(ab[rpt[i]:rpt[i + 1]].sum()), rel=1e-13, abs=0.0)
 
 
 def test_row_window_matches_full():
