@@ -131,6 +131,7 @@ cudaError_t launch_scan(int64_t *crpt, int64_t n, long long *tile_sums, cudaStre
 int64_t bin_tile_rows();
 cudaError_t launch_iota(int32_t *out, int64_t n, cudaStream_t s);
 
+
 // --- symbolic.cu / numeric.cu -------------------------------------------------
 int sym_kernel_count();
 int num_kernel_count();

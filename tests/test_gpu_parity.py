@@ -380,10 +380,43 @@ def _check_rows(A, B, sampled):
         assert_values_close(val, oval, ab, what=f"row {i}")
 
 
+def device_row_checks(C, r0, cnt_o, cs_o, vs_o, ab_o, what):
+    """Every row of a device C (rows r0.. of the product) against the
+    oracle's row checksums: size and sum of columns exactly, columns
+    strictly increasing inside each row, and the sum of values within
+    1e-12 of the row's sum of |a*b| plus the rounding of the two row sums
+    (2 n u times the row's sum of |values|)."""
+    rpt = C.rpt
+    n = rpt.numel() - 1
+    cnt = (rpt[1:] - rpt[:-1]).cpu().numpy()
+    assert np.array_equal(cnt, cnt_o[r0:r0 + n]), f"{what}: row sizes"
+    if C.nnz == 0:
+        return
+    col = C.col.long()
+    csum = torch.zeros(C.nnz + 1, dtype=torch.int64, device=col.device)
+    torch.cumsum(col, 0, out=csum[1:])
+    cs = (csum[rpt[1:]] - csum[rpt[:-1]]).cpu().numpy()
+    assert np.array_equal(cs, cs_o[r0:r0 + n]), f"{what}: column sums"
+    inc = col[1:] > col[:-1]
+    starts = torch.zeros(C.nnz, dtype=torch.bool, device=col.device)
+    starts[rpt[1:-1][rpt[1:-1] < C.nnz]] = True
+    assert bool((inc | starts[1:]).all()), f"{what}: columns not strictly increasing inside a row"
+    del inc, starts, csum
+    rowid = torch.repeat_interleave(torch.arange(n, device=col.device), rpt[1:] - rpt[:-1],
+                                    output_size=C.nnz)
+    vs = torch.zeros(n, dtype=torch.float64, device=col.device).index_add_(0, rowid, C.val).cpu().numpy()
+    av = torch.zeros(n, dtype=torch.float64, device=col.device).index_add_(0, rowid, C.val.abs()).cpu().numpy()
+    del rowid
+    u = np.finfo(np.float64).eps / 2
+    tol = 1e-12 * ab_o[r0:r0 + n] + 2 * cnt * u * av
+    bad = np.abs(vs - vs_o[r0:r0 + n]) > tol
+    assert not bad.any(), f"{what}: row value sums, first row {r0 + int(np.nonzero(bad)[0][0])}"
+
+
 @pytest.mark.slow
 def test_full_size_stencil27_128(handle):
-    """The 27-point stencil on 128^3 (n = 2,097,152): closed-form totals,
-    every row's size against the oracle, sampled rows' values."""
+    """The 27-point stencil on 128^3 (n = 2,097,152): closed-form totals and
+    the whole C against the oracle element by element (254.8M entries)."""
     s = 128
     A = W.stencil27(s, seed=3)
     dA = to_dev(A)
@@ -391,30 +424,40 @@ def test_full_size_stencil27_128(handle):
     handle.status()
     assert C.nnz == (5 * s - 6) ** 3 == 254840104
     assert handle.stats()["total_nprod"] == (9 * s - 10) ** 3 == 1489355288
-    want = oracle.symbolic(A, A)
-    rpt = C.rpt.cpu().numpy()
-    assert np.array_equal(np.diff(rpt), want)
-    rng = np.random.default_rng(0)
-    rows = sorted(set(rng.integers(0, A.rows, 300).tolist()) | {0, A.rows - 1, A.rows // 2})
-    _, sampled = _sample_rows(C, rows)
-    _check_rows(A, A, sampled)
+    g_rpt, g_col, g_val = C.numpy()
+    del C
+    rpt, col, val, ab = oracle.spgemm(A, A, threads=oracle.max_threads())
+    assert np.array_equal(g_rpt, rpt)
+    assert np.array_equal(g_col, col)
+    assert_values_close(g_val, val, ab)
 
 
 @pytest.mark.slow
 def test_full_size_rmat_2_20(handle):
     """R-MAT n = 2^20, degree 16, C ~ 9.7e9 entries (int64 C.rpt): every
-    row's size against the oracle, sampled and heaviest rows' values."""
+    row's size, sum of columns and sum of values against the oracle's row
+    checksums (C does not fit host memory, so rows are compared by these),
+    computed in eight row slabs of about equal products so each slab's
+    checks fit the device beside it, then the values of sampled and the
+    heaviest rows in full."""
+    from paper_2206_07244_gb300 import shard
     A = W.rmat(20, 16, seed=1)
     dA = to_dev(A)
-    C = handle.multiply(dA, dA)
-    handle.status()
-    want = oracle.symbolic(A, A)
-    rpt = C.rpt.cpu().numpy()
-    assert C.nnz == int(want.sum()) > 2**31
-    assert np.array_equal(np.diff(rpt), want)
+    cnt_o, cs_o, vs_o, ab_o = oracle.row_checksums(A, A, threads=oracle.max_threads())
+    assert int(cnt_o.sum()) > 2**31
     rng = np.random.default_rng(1)
-    heavy = np.argsort(want)[-8:].tolist()
+    heavy = np.argsort(cnt_o)[-8:].tolist()
     rows = sorted(set(rng.integers(0, A.rows, 200).tolist()) | set(heavy))
-    _, sampled = _sample_rows(C, rows)
-    del C
+    sampled = {}
+    for r0, r1 in shard.slab_bounds(oracle.nprod(A, A), 8):
+        handle.symbolic(dA, dA, r0, r1)
+        C = handle.numeric(dA, dA)
+        handle.status()
+        device_row_checks(C, r0, cnt_o, cs_o, vs_o, ab_o, f"R-MAT 2^20 rows {r0}:{r1}")
+        mine = [i for i in rows if r0 <= i < r1]
+        _, got = _sample_rows(C, [i - r0 for i in mine])
+        sampled.update({i + r0: v for i, v in got.items()})
+        del C
+        torch.cuda.empty_cache()
+    assert len(sampled) == len(rows)
     _check_rows(A, A, sampled)

@@ -1,10 +1,10 @@
 """Parity at the full sizes of the two benchmark workloads that the other GPU
 tests cover only in small:
 
-- learned sizing (trained predictor) on the row slab of the held-out R-MAT
-  n = 2^21, degree 32 (seed 2021) that the benchmark times: every row size
-  against the oracle's symbolic count, and the values of sampled rows, the
-  heaviest among them;
+- learned sizing (trained predictor) on a row slab of the held-out R-MAT
+  n = 2^21, degree 32 (seed 2021): every row's size, sum of columns and sum
+  of values against the oracle's row checksums, and the values of sampled
+  rows, the heaviest among them, in full;
 - the batch of 512 multigrid Galerkin products P^T (A P) (sides uniform in
   [8, 48], seed 0, every product with its own inputs) in one persistent
   launch: all 1,024 products against the oracle, bit for bit (integer
@@ -63,6 +63,7 @@ def test_learned_sizing_held_out_rmat_2_21_slab():
     man = json.load(open(learned.MANIFEST))
     theta = np.load(learned.WEIGHTS)
     dA = ops.CSR.from_workload(A)
+    cnt_o, cs_o, vs_o, ab_o = oracle.row_checksums(A, A, r0, r1, threads=oracle.max_threads())
     with ops.Handle() as h:
         h.set_predictor(theta, man["margin"])
         h.set_mode("learned")
@@ -73,6 +74,9 @@ def test_learned_sizing_held_out_rmat_2_21_slab():
         rpt = C.rpt.cpu().numpy()
         assert rpt[0] == 0
         assert np.array_equal(np.diff(rpt), sizes), "row sizes differ from the oracle"
+        # every row of the slab: sizes, column sums, value sums
+        from test_gpu_parity import device_row_checks
+        device_row_checks(C, 0, cnt_o, cs_o, vs_o, ab_o, "held-out slab")
         for i in rows:
             s, e = int(rpt[i]), int(rpt[i + 1])
             _, ocol, oval, oab = oracle.spgemm(A, A, r0 + i, r0 + i + 1)
