@@ -228,6 +228,35 @@ def test_trained_network_gain():
     assert t_learned < 0.9 * t_bound
 
 
+@pytest.mark.slow
+def test_trained_network_beats_plain_on_stencil_128():
+    # The committed network against the exact symbolic pass on the 27-point
+    # stencil 128^3, whose rows all fit the hash tables: the one-phase rows
+    # skip the symbolic hashing, and after the load feedback settles the
+    # learned path must be faster than the plain one (median of 5 calls).
+    # Rows past the last hash table (the power-law rows of R-MAT) take the
+    # exact bitmap path in both modes, so there the network has nothing to act on.
+    if not os.path.exists(learned.WEIGHTS):
+        pytest.skip("no trained weights")
+    theta = np.load(learned.WEIGHTS)
+    margin = json.load(open(learned.MANIFEST))["margin"]
+    A = W.stencil27(128, seed=3)
+    dA = dev(A)
+    with ops.Handle() as h:
+        t_plain = _median_ms(h, dA, reps=6)
+        h.set_predictor(theta, margin)
+        h.set_mode("learned")
+        for _ in range(3):   # the load feedback settles
+            C = h.multiply(dA, dA)
+            del C
+        t_learned = _median_ms(h, dA, reps=6)
+        st = h.learned_stats()
+    print(f"stencil 128^3: plain {t_plain:.3f} ms, learned {t_learned:.3f} ms "
+          f"({t_plain / t_learned:.3f}x), stats {st}")
+    assert st["one_phase_rows"] > 0.9 * A.rows
+    assert t_learned < t_plain
+
+
 def test_load_feedback_factor():
     # A network that predicts size 1 for every row: the first call's one-phase
     # rows all overflow, so each later call doubles the factor of their class
