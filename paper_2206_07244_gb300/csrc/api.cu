@@ -90,6 +90,7 @@ struct spgemm_handle {
     long long num_size[kMaxBins] = {};
     RunPlan rplan;               // windowed pass 2 plan of the last symbolic call
     bool b_unsorted = false;     // some row of B has decreasing columns
+    bool b_distinct = false;     // every row of B has strictly increasing columns
     // the last plain numeric call's rows stay in their bins (numeric order)
     // until the next symbolic call: spgemm_numeric_values runs them again
     bool reuse = false;
@@ -572,6 +573,7 @@ int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *s
         w.lanes = phase ? h->cfg.num_lanes_per_brow : h->cfg.lanes_per_brow;
         w.unroll = h->cfg.bitmap_unroll;
         w.multi = h->cfg.hash_access;
+        w.distinct = phase == 1 && h->b_distinct;
         w.err = d_err(h);
         const KernelDesc &d = phase ? num_kernel(kid[j]) : sym_kernel(kid[j]);
         size_t smem = 0;
@@ -827,6 +829,7 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
     CK(cudaMemcpyAsync(h_fb, L.fb, sizeof(unsigned long long) * kFbCounters, cudaMemcpyDeviceToHost, s));
     if ((rc = read_counters(h))) return rc;
     h->b_unsorted = (h->h_cnt[1].flags & 1ull) != 0;
+    h->b_distinct = false;
     *nnz_out = static_cast<int64_t>(h->h_cnt[1].total);
     h->lstats[0] = 0;
     for (int j = 0; j < last; ++j) h->lstats[0] += h->lsize[j];
@@ -1113,7 +1116,9 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     if (note(launch_nprod(op, crpt, h->sm_count * 8, h->stream)) != cudaSuccess) return fail(SPGEMM_ERR_CUDA);
     time_end(h, kSlotNprod, h->stream);
     h->rplan = run_plan(h->cfg, h->smem_dyn_max, B->cols);
-    if ((h->rplan.lists > 0 || h->wp_on) && !h->split_on &&
+    // B's column order: the windowed kernels need sorted rows, the warp-row
+    // numeric hash kernels skip value atomics when columns are distinct
+    if (!h->split_on &&
         note(launch_sorted_check(op, B->rows, B->nnz, d_counters(h, 1), h->sm_count * 4, h->stream)) !=
             cudaSuccess)
         return fail(SPGEMM_ERR_CUDA);
@@ -1168,6 +1173,7 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     time_end(h, kSlotNumPass1, h->stream);
     if ((rc = read_counters(h))) return fail(rc);
     h->b_unsorted = (h->h_cnt[1].flags & 1ull) != 0;
+    h->b_distinct = (h->h_cnt[1].flags & 3ull) == 0;
     h->nwin = static_cast<long long>(h->h_cnt[1].windows);
     h->nwin_col = static_cast<long long>(h->h_cnt[1].wcol);
     h->stats[2] = static_cast<int64_t>(h->h_cnt[1].total);

@@ -485,7 +485,13 @@ namespace ops {
 // shuffles under the group's own lane mask: groups of one warp may pick
 // different S and run different trip counts. S must be the same on every
 // lane of a group. Calls f(key, a_value, b_value).
-template <int TPR, bool NEED_VAL, typename F>
+// SYNC: the group synchronises after every piece, and its lanes run the
+// same trip counts (pieces are stepped from 0 for the whole group), so a
+// caller whose products of one piece are distinct (one B row per step,
+// S == TPR, no repeated column in a B row) may update its table without
+// atomics: no two lanes of a step touch the same entry, and a step sees the
+// writes of the steps before it.
+template <int TPR, bool NEED_VAL, bool SYNC = false, typename F>
 __device__ __forceinline__ void group_row_walk(const Operands &op, int64_t p0, int64_t p1, int S,
                                                F &&f) {
     static_assert(TPR <= 32, "group walk is for sub-warp row groups");
@@ -509,18 +515,37 @@ __device__ __forceinline__ void group_row_walk(const Operands &op, int64_t p0, i
             const long long q0 = __shfl_sync(gm, my_q0, src);
             const int len = __shfl_sync(gm, my_len, src);
             const double a = NEED_VAL ? __shfl_sync(gm, my_a, src) : 0.0;
-            for (int off = ls; off < len; off += S * kPieceIters) {
-                int key[kPieceIters];
-                double bv[kPieceIters];
+            if constexpr (SYNC) {
+                // the group's longest row sets the trip count (one B row per
+                // step when S == TPR: every lane sees the same len)
+                for (int off0 = 0; off0 < len; off0 += S * kPieceIters) {
+                    int key[kPieceIters];
+                    double bv[kPieceIters];
 #pragma unroll
-                for (int u = 0; u < kPieceIters; ++u) {
-                    const int o = off + u * S;
-                    key[u] = o < len ? __ldg(op.bcol + q0 + o) : -1;
-                    bv[u] = (NEED_VAL && o < len) ? __ldg(op.bval + q0 + o) : 0.0;
+                    for (int u = 0; u < kPieceIters; ++u) {
+                        const int o = off0 + ls + u * S;
+                        key[u] = o < len ? __ldg(op.bcol + q0 + o) : -1;
+                        bv[u] = (NEED_VAL && o < len) ? __ldg(op.bval + q0 + o) : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kPieceIters; ++u)
+                        if (key[u] >= 0) f(key[u], a, bv[u]);
+                    __syncwarp(gm);
                 }
+            } else {
+                for (int off = ls; off < len; off += S * kPieceIters) {
+                    int key[kPieceIters];
+                    double bv[kPieceIters];
 #pragma unroll
-                for (int u = 0; u < kPieceIters; ++u)
-                    if (key[u] >= 0) f(key[u], a, bv[u]);
+                    for (int u = 0; u < kPieceIters; ++u) {
+                        const int o = off + u * S;
+                        key[u] = o < len ? __ldg(op.bcol + q0 + o) : -1;
+                        bv[u] = (NEED_VAL && o < len) ? __ldg(op.bval + q0 + o) : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kPieceIters; ++u)
+                        if (key[u] >= 0) f(key[u], a, bv[u]);
+                }
             }
         }
     }

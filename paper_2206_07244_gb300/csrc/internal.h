@@ -46,6 +46,8 @@ struct BinWork {
     int lanes;            // threads per B row, 0 = per-row automatic
     int unroll;           // bitmap kernels: products in flight per lane (4 or 8; 0 = 4)
     int multi;            // plain hash kernels: read a slot before its compare-and-swap
+    int distinct;         // every row of B has distinct columns (checked): warp-row numeric
+                          // hash kernels may update values without atomics
     int *err;             // device error word
     // numeric bitmap kernel, pass 2 by column windows (B rows sorted)
     const int32_t *bs;    // run boundaries of B rows at the sub-ranges (G + 1 per row), or nullptr
@@ -92,7 +94,7 @@ struct Counters {
     unsigned long long bin_nnza[kMaxBins];  // pass 1: A entries of the bin's rows
     unsigned long long max_size;
     unsigned long long total;
-    unsigned long long flags;         // bit 0: some row of B has decreasing columns
+    unsigned long long flags;         // bit 0: some row of B has decreasing columns; bit 1: repeated ones
     unsigned long long windows;       // column windows of the large rows (win_count_kernel)
     unsigned long long wcol;          // those of them that accumulate by column
 };

@@ -58,6 +58,25 @@ __device__ __forceinline__ bool num_insert(int *tk, double *tv, int key, double 
     return false;
 }
 
+// The same probe with the value updated by a plain read, fused
+// multiply-add and write: for row groups whose steps touch distinct entries
+// only (group_row_walk with SYNC), where no other thread can update the
+// entry in between. The key still takes a compare-and-swap: distinct keys of
+// one step may probe the same slot.
+template <int T>
+__device__ __forceinline__ bool num_insert_owned(int *tk, double *tv, int key, double a, double b) {
+    uint32_t h = hash_slot<T>(key);
+    for (int it = 0; it < T; ++it) {
+        const int old = atomicCAS(tk + h, -1, key);
+        if (old == -1 || old == key) {
+            tv[h] = fma(a, b, tv[h]);
+            return true;
+        }
+        h = next_slot<T>(h);
+    }
+    return false;
+}
+
 // Mean referenced B-row length decides how many threads walk one B row; the
 // symbolic phase's n_prod is gone by now (C.rpt holds offsets), so the row
 // group recomputes it from B.rpt (those lines are needed right after).
@@ -188,6 +207,11 @@ num_hash_kernel(Operands op, BinWork w) {
             smem_raw + (sizeof(int) + sizeof(double)) * (size_t)RPB * T);
         block_row_walk<BLOCK, true>(op, p0, p1, S, sc, [&](int key, double a, double b) {
             if (!num_insert<T, MULTI>(tk, tv, key, a, b)) failed = true;
+        });
+    } else if (!MULTI && w.distinct && S == TPR) {
+        // one B row per step, its columns distinct: values without atomics
+        group_row_walk<TPR, true, true>(op, p0, p1, S, [&](int key, double a, double b) {
+            if (!num_insert_owned<T>(tk, tv, key, a, b)) failed = true;
         });
     } else {
         group_row_walk<TPR, true>(op, p0, p1, S, [&](int key, double a, double b) {

@@ -220,8 +220,11 @@ cudaError_t launch_bin_pass2(const int64_t *sizes, int64_t n, const Ranges &rg,
 }
 
 // ---------------------------------------------------------------------------
-// Is every row of B sorted by column? (The column-window numeric kernel walks
-// B rows with cursors and needs non-decreasing columns.) Work is split over
+// Is every row of B sorted by column (bit 0 of flags set when not), and
+// are its columns distinct (bit 1 set when a row repeats a column)? The
+// column-window kernels need non-decreasing rows; the warp-per-row numeric
+// hash kernels update values without atomics when the columns of every B
+// row are distinct. Work is split over
 // B's non-zeros; each thread checks the pairs (e, e + 1) of its entries that
 // lie in one row.
 constexpr int kSortItems = 8;
@@ -229,7 +232,7 @@ constexpr int kSortItems = 8;
 __global__ void __launch_bounds__(kBinBlock)
 sorted_check_kernel(Operands op, int64_t brows, int64_t bnnz, Counters *cnt) {
     const int64_t tile = static_cast<int64_t>(blockDim.x) * kSortItems;
-    bool bad = false;
+    bool bad = false, dup = false;
     for (int64_t base = static_cast<int64_t>(blockIdx.x) * tile; base < bnnz - 1;
          base += static_cast<int64_t>(gridDim.x) * tile) {
         const int64_t e0 = base + static_cast<int64_t>(threadIdx.x) * kSortItems;
@@ -243,10 +246,16 @@ sorted_check_kernel(Operands op, int64_t brows, int64_t bnnz, Counters *cnt) {
                 row = upper_bound_rpt(op.brpt, op.b64, row + 1, brows, e);
                 next = ld_rpt(op.brpt, op.b64, row + 1);
             }
-            if (e + 1 < next && __ldg(op.bcol + e + 1) < __ldg(op.bcol + e)) bad = true;
+            if (e + 1 < next) {
+                const int c0 = __ldg(op.bcol + e), c1 = __ldg(op.bcol + e + 1);
+                bad |= c1 < c0;
+                dup |= c1 == c0;
+            }
         }
     }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31u) == 0) atomicOr(&cnt->flags, 1ull);
+    const bool any_bad = __any_sync(0xffffffffu, bad), any_dup = __any_sync(0xffffffffu, dup);
+    if ((threadIdx.x & 31u) == 0 && (any_bad || any_dup))
+        atomicOr(&cnt->flags, (any_bad ? 1ull : 0ull) | (any_dup ? 2ull : 0ull));
 }
 
 cudaError_t launch_sorted_check(const Operands &op, int64_t brows, int64_t bnnz, Counters *cnt,
