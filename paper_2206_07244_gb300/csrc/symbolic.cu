@@ -138,7 +138,10 @@ sym_bitmap_kernel(Operands op, BinWork w, int words) {
             rsel.c0 = 0;
             rsel.c1 = INT_MAX;
         }
-        block_row_walk<kBmBlock, false, ITERS, 0, RUNS>(op, p0, p1, S, sc, [&](int key, double, double) {
+        // column loads only: 8 per lane at once in 1024-thread blocks (one
+        // block per SM, latency bound)
+        constexpr int kIt = BLOCK == 1024 && ITERS < 8 ? 8 : ITERS;
+        block_row_walk<kBmBlock, false, kIt, 0, RUNS>(op, p0, p1, S, sc, [&](int key, double, double) {
             const unsigned rel = static_cast<unsigned>(key - c0i);   // one compare covers both ends
             if (rel < span32) atomicOr(bm + (rel >> 5), 1u << (rel & 31));
         }, &rsel);
