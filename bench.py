@@ -818,10 +818,22 @@ def main():
     # ceilings count
     is_num_bitmap = 16 <= k < 32 and k - 16 == len(h.get_config()["num_kernel"]) - 1
     kernel_products = None
+    phases = None
     if is_num_bitmap:
+        # the same untimed step with the kernel's phase clocks on: SM clock
+        # cycles of each phase summed over the launch's blocks
+        h.set_phase_clocks(True)
         C = step()
+        clk_ph = h.bitmap_phase_clocks(reset=True)
+        h.set_phase_clocks(False)
         nnz_row = np.diff(C.rpt.cpu().numpy())
         del C
+        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+        tot = max(sum(clk_ph.values()), 1)
+        phases = {"sm_cycles": clk_ph, "frac": {k: round(v / tot, 4) for k, v in clk_ph.items()},
+                  "mean_sm_cycles_per_launch": int(tot / n_sm),
+                  "note": "one untimed step with a block barrier ending each phase; thread 0 of every "
+                          "block adds its SM clock cycles per phase"}
         cut = h.get_config()["num_range"][-2] if len(h.get_config()["num_range"]) > 1 else -1
         cs = np.concatenate([[0], np.cumsum(np.diff(rpt64)[A.col])])
         row_np = cs[rpt64[1:]] - cs[rpt64[:-1]]
@@ -857,6 +869,8 @@ def main():
             roofline["atomic_peak_gops"] = rates["l2_red_scattered_gops"]
             roofline["fp64_frac"] = round(prate / rates["fp64_fma_gops"], 4)
             roofline["fp64_peak_gops"] = rates["fp64_fma_gops"]
+    if phases:
+        roofline["phases"] = phases
     whole = {"bytes_per_step": int(total_bytes),
              "achieved_gbs": round(total_bytes / (ms / args.steps / 1e3) / 1e9, 2),
              "frac": round(total_bytes / (ms / args.steps / 1e3) / 1e9 / peak, 4)}

@@ -280,6 +280,25 @@ int spgemm_set_timing(spgemm_handle *h, int enable);
 int spgemm_kernel_times(spgemm_handle *h, double *ms, int64_t *launches, int n,
                         int reset);
 
+/* Phase clocks of the numeric bitmap kernel: a profiling aid with no
+ * counterpart in the paper. With enable != 0, numeric calls from then on run
+ * the 1024-thread, whole-row form of that kernel with a block barrier at the
+ * end of each phase, and thread 0 of every block adds the SM clock cycles
+ * its block spent in the phase to counters kept by the handle (a 56-byte
+ * device buffer allocated at the first enable, freed by spgemm_destroy);
+ * enable = 0 turns the barriers and counters off. C does not depend on it.
+ * spgemm_bitmap_phase_clocks synchronises the handle's stream and writes
+ * min(n, 7) int64 sums over blocks, one per phase in order: bitmap clear,
+ * pass 1 (column bits), per-word prefix counts, C.col write, C.val clear,
+ * pass 2 (float64 reductions into C.val), L2 priority reset of the row's
+ * C.val lines; all 0 before the first enable. reset != 0 clears them. Cycles
+ * of one SM's clock: divide the sum by the SM count and the clock rate for
+ * the time each phase takes when all SMs run the kernel. Errors:
+ * SPGEMM_ERR_INVALID (null handle, n < 0, null out with n > 0),
+ * SPGEMM_ERR_OOM, SPGEMM_ERR_CUDA. */
+int spgemm_set_phase_clocks(spgemm_handle *h, int enable);
+int spgemm_bitmap_phase_clocks(spgemm_handle *h, int64_t *out, int n, int reset);
+
 /* Per-phase statistics of the last symbolic/numeric call: 4 + 2 * NB
  * int64 values: total n_prod, max row n_prod, total n_nz, max row n_nz,
  * then the symbolic and numeric bin sizes (SPGEMM_MAX_BINS each). */

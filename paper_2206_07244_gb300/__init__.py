@@ -253,6 +253,19 @@ class Handle:
                 "cell_log2": v[4], "cells": v[5], "budget": v[6], "whole_width_max": v[7],
                 "split": bool(v[8])}
 
+    PHASES = ("bitmap_clear", "pass1_columns", "prefix_counts", "ccol_write", "cval_clear",
+              "pass2_reductions", "priority_reset")
+
+    def set_phase_clocks(self, enable: bool) -> None:
+        """Per-phase SM clock sums of the numeric bitmap kernel (profiling)."""
+        _abi.check(self._lib.spgemm_set_phase_clocks(self._h, int(bool(enable))), "spgemm_set_phase_clocks")
+
+    def bitmap_phase_clocks(self, reset: bool = True) -> dict:
+        arr = (ctypes.c_int64 * len(self.PHASES))()
+        _abi.check(self._lib.spgemm_bitmap_phase_clocks(self._h, arr, len(self.PHASES), int(bool(reset))),
+                   "spgemm_bitmap_phase_clocks")
+        return dict(zip(self.PHASES, list(arr)))
+
     def status(self) -> None:
         _abi.check(self._lib.spgemm_status(self._h), "spgemm_status")
 

@@ -22,7 +22,7 @@ EXPORTS = [
     "spgemm_destroy", "spgemm_last_stats", "spgemm_kernel_info", "spgemm_strerror",
     "spgemm_last_cuda_error",
     "spgemm_multiply_host", "spgemm_bin_stats", "spgemm_window_stats", "spgemm_set_timing",
-    "spgemm_kernel_times",
+    "spgemm_kernel_times", "spgemm_set_phase_clocks", "spgemm_bitmap_phase_clocks",
     "spgemm_rowptr_noalloc", "spgemm_mlp_param_count", "spgemm_set_predictor", "spgemm_set_mode",
     "spgemm_learned_stats", "spgemm_features", "spgemm_mlp_forward", "spgemm_mlp_train_step",
     "spgemm_mlp_adam", "spgemm_batch_create", "spgemm_batch_run", "spgemm_batch_sync",
@@ -124,6 +124,8 @@ def lib(path: str | None = None):
                                 ctypes.c_float, ctypes.c_float, P],
             "spgemm_kernel_times": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64),
                                     ctypes.c_int, ctypes.c_int],
+            "spgemm_set_phase_clocks": [P, ctypes.c_int],
+            "spgemm_bitmap_phase_clocks": [P, ctypes.POINTER(I64), ctypes.c_int, ctypes.c_int],
         }
         for name, args in sig.items():
             f = getattr(L, name)

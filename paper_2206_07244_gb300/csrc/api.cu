@@ -146,6 +146,9 @@ struct spgemm_handle {
     size_t stage_rpt_n = 0;
     bool timing = false;
     bool serial = false;   // timing mode 2: every bin kernel on the main stream, one after another
+    // phase clocks of the numeric bitmap kernel (profiling; off unless requested)
+    bool phase_clk = false;
+    unsigned long long *d_clk = nullptr;   // kPhaseClocks sums
     cudaEvent_t t0[kSlots] = {}, t1[kSlots] = {};
     bool pending[kSlots] = {};
     double ms[kSlots] = {};
@@ -574,6 +577,7 @@ int run_bins(spgemm_handle *h, int phase, const Operands &op, const long long *s
         w.unroll = h->cfg.bitmap_unroll;
         w.multi = h->cfg.hash_access;
         w.distinct = phase == 1 && h->b_distinct;
+        w.clk = phase == 1 && h->phase_clk ? h->d_clk : nullptr;
         w.err = d_err(h);
         const KernelDesc &d = phase ? num_kernel(kid[j]) : sym_kernel(kid[j]);
         size_t smem = 0;
@@ -1723,6 +1727,31 @@ int spgemm_set_timing(spgemm_handle *h, int enable) {
     return SPGEMM_OK;
 }
 
+int spgemm_set_phase_clocks(spgemm_handle *h, int enable) {
+    if (!h) return SPGEMM_ERR_INVALID;
+    if (enable && !h->d_clk) {
+        h->d_clk = static_cast<unsigned long long *>(dev_alloc(h, sizeof(unsigned long long) * kPhaseClocks));
+        if (!h->d_clk) return SPGEMM_ERR_OOM;
+        if (cudaMemsetAsync(h->d_clk, 0, sizeof(unsigned long long) * kPhaseClocks, h->stream) != cudaSuccess)
+            return SPGEMM_ERR_CUDA;
+    }
+    h->phase_clk = enable != 0;
+    return SPGEMM_OK;
+}
+
+int spgemm_bitmap_phase_clocks(spgemm_handle *h, int64_t *out, int n, int reset) {
+    if (!h || n < 0 || (n > 0 && !out)) return SPGEMM_ERR_INVALID;
+    unsigned long long v[kPhaseClocks] = {};
+    if (h->d_clk) {
+        if (cudaMemcpyAsync(v, h->d_clk, sizeof(v), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            (reset && cudaMemsetAsync(h->d_clk, 0, sizeof(v), h->stream) != cudaSuccess) ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return SPGEMM_ERR_CUDA;
+    }
+    for (int k = 0; k < n && k < kPhaseClocks; ++k) out[k] = static_cast<int64_t>(v[k]);
+    return SPGEMM_OK;
+}
+
 int spgemm_kernel_times(spgemm_handle *h, double *ms, int64_t *launches, int n, int reset) {
     if (!h || n < 0) return SPGEMM_ERR_INVALID;
     CK(cudaStreamSynchronize(h->stream));
@@ -1783,6 +1812,7 @@ int spgemm_destroy(spgemm_handle *h) {
     dev_free(h, h->wcells);
     dev_free(h, h->wcslot);
     dev_free(h, h->wspill);
+    dev_free(h, h->d_clk);
     if (h->side[0]) cudaStreamSynchronize(h->stream);
     for (int i = 0; i < kSide; ++i) {
         if (h->side[i]) cudaStreamDestroy(h->side[i]);

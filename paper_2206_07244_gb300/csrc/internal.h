@@ -79,7 +79,13 @@ struct BinWork {
     // symbolic bitmap kernel: bit 0 set = some row of B is not sorted (the
     // runs are then not used); nullptr = B known sorted
     const unsigned long long *bflags;
+    // numeric bitmap kernel (whole-row form): per-phase SM clock sums
+    // (kPhaseClocks), or nullptr; a profiling aid
+    unsigned long long *clk;
 };
+
+// Phases of the numeric bitmap kernel that spgemm_bitmap_phase_clocks reports.
+constexpr int kPhaseClocks = 7;
 
 struct Ranges {
     long long r[kMaxBins];

@@ -533,6 +533,21 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
     unsigned *bm32 = reinterpret_cast<unsigned *>(bm);   // same words, 32-bit halves
     unsigned *pre = reinterpret_cast<unsigned *>(bm + words);
     __shared__ unsigned sw[33];
+    // phase clocks (profiling, w.clk set; 1024-thread blocks, whose
+    // registers have room): a block barrier ends each phase, then thread 0
+    // adds the SM clock cycles since the previous mark
+    constexpr bool kClk = BLOCK == 1024;
+    long long tmark = 0;
+    if (kClk && w.clk && threadIdx.x == 0) tmark = clock64();
+    auto phase_end = [&](int k) {
+        if (!kClk || !w.clk) return;   // uniform: a kernel argument
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const long long t = clock64();
+            atomicAdd(w.clk + k, static_cast<unsigned long long>(t - tmark));
+            tmark = t;
+        }
+    };
     const int64_t row = w.bins ? static_cast<int64_t>(w.bins[w.off + blockIdx.x])
                                : w.off + static_cast<int64_t>(blockIdx.x);
     const int64_t cbase = w.crpt[row];
@@ -551,6 +566,7 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
         const int nw = static_cast<int>(((op.ncols - c0 < span ? op.ncols - c0 : span) + 63) / 64);
         for (int i = threadIdx.x; i < nw; i += kBmBlock) bm[i] = 0ull;
         __syncthreads();
+        phase_end(0);
         // pass 1: the row's columns inside this window. 32-bit atomics on the
         // two halves of a 64-bit word: shared 64-bit atomics run several
         // times slower on this GPU
@@ -562,11 +578,13 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
             const unsigned rel = static_cast<unsigned>(key - c0i);   // one compare covers both ends
             if (rel < span32) atomicOr(bm32 + (rel >> 5), 1u << (rel & 31));
         }, &rsel);
+        phase_end(1);
         // per-word prefix counts = rank of a word's first column in the
         // window. Warps own contiguous ranges of words and their lanes read
         // consecutive words (no bank conflicts): a warp scan per 32 words,
         // one block scan of the warp totals.
         const unsigned run = bitmap_ranks<kBmBlock>(bm, pre, nw, sw);
+        phase_end(2);
         const int64_t cnt = run;
         if (done + cnt > n_expect) ok = false;   // uniform: cnt and done are block-wide
         if (ok) {
@@ -586,8 +604,15 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
             // them; denser words are written by the whole warp, one word at a
             // time with one lane per bit, so that each store covers one run
             // of consecutive entries of C.col (measured: 1.5% faster than
-            // every lane writing its own word, on R-MAT n = 2^20).
-            constexpr int kDenseWord = 24;
+            // every lane writing its own word, on R-MAT n = 2^20). The
+            // write is bound by instruction issue: a lane loop runs as often
+            // as the fullest word of the 32 asks, so words of 12 columns or
+            // more go to the whole warp (R-MAT n = 2^20 rows: 8.0 instead of
+            // 9.2 loop trips per 32 words; this phase 3.6% faster than with
+            // 24). Entry-parallel rounds (lane e finds the word of entry e by
+            // a shuffle search) store fully coalesced but issue more: 27%
+            // slower.
+            constexpr int kDenseWord = 12;
             constexpr unsigned long long kWordCost = 2;
             const int lane = threadIdx.x & 31;
             const unsigned lt = (1u << lane) - 1u;
@@ -637,6 +662,7 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
                     if ((hi >> lane) & 1u) ccol[pw + __popc(lo) + __popc(hi & lt)] = cb + 32 + lane;
                 }
             }
+            phase_end(3);
             const unsigned long long pol = l2_evict_last_policy();
             const int nl = static_cast<int>(p1 - p0 < INT32_MAX ? p1 - p0 : INT32_MAX);
             // one thread per A entry: the row's A entries must fit the block
@@ -704,6 +730,7 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
             }
             for (int64_t t = threadIdx.x; t < cnt; t += kBmBlock) st_keep(cval + t, 0.0, pol);
             __syncthreads();
+            phase_end(4);
             // pass 2: each product lands on its column's rank (the walk
             // scratch of pass 1 is still in place)
             block_row_walk<kBmBlock, true, ITERS, 2, RUNS>(op, p0, p1, S, sc, [&](int key, double a, double b) {
@@ -718,12 +745,14 @@ num_bitmap_kernel(Operands op, BinWork w, int words) {
                 }
             }, &rsel);
             __syncthreads();
+            phase_end(5);
             // back to normal priority: every 128-byte line the segment touches
             const uintptr_t l0 = reinterpret_cast<uintptr_t>(cval) & ~static_cast<uintptr_t>(127);
             const uintptr_t l1 = reinterpret_cast<uintptr_t>(cval + cnt);
             for (uintptr_t l = l0 + 128 * static_cast<uintptr_t>(threadIdx.x); l < l1;
                  l += 128 * static_cast<uintptr_t>(kBmBlock))
                 l2_priority_normal(reinterpret_cast<const void *>(l));
+            phase_end(6);
         }
         done += cnt;
         __syncthreads();
