@@ -72,8 +72,11 @@ NSLOTS = len(SLOT_NAMES)
 # intermediate products. Each entry records the hash of the kernel sources at
 # capture time; a kernel changed since then reports no traffic.
 TRAFFIC_WINDOWED = {
-    # ("rmat20", "num_bitmap_kernel"): {"rows": "R0:R1", "dram_bytes": B,
-    #     "window_products": P, "sources_sha": "..."},
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum of the launch for the
+    # row window 4096:8192 (--rows 4096:8192, the timed step's launch),
+    # taken with the kernel sources whose hash is sources_sha
+    ("rmat20", "num_bitmap_kernel"): {"rows": "4096:8192", "dram_bytes": 19445754112,
+                                      "window_products": 635646019, "sources_sha": "386917a40f7f8a0b"},
 }
 KERNEL_SOURCES = ["paper_2206_07244_gb300/csrc/numeric.cu", "paper_2206_07244_gb300/csrc/common.cuh"]
 
