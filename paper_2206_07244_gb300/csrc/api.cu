@@ -734,6 +734,9 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
     CK(launch_bin_pass1(L.lsizes, mw, rn, op, d_counters(h, 0), nullptr, s));
     time_end(h, kSlotMlp, s);
     if ((rc = read_counters(h))) return rc;
+    // B's column order (checked before this call): distinct columns let the
+    // warp-row one-phase kernels update values without atomics
+    h->b_distinct = (h->h_cnt[1].flags & 3ull) == 0;
     h->lid = plan_bins(h->h_cnt[0], nb, h->lsize, h->loff);
     if (!h->lid) CK(launch_bin_pass2(L.lsizes, mw, rn, h->loff, d_counters(h, 0), d_bins(h), s));
     // the exact list starts with the rows of the bitmap bin
@@ -775,6 +778,7 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
         w.cnt = h->lsize[j];
         w.crpt = crpt;
         w.lanes = h->cfg.num_lanes_per_brow;
+        w.distinct = h->b_distinct;
         w.err = d_err(h);
         w.tcol = h->tcol; w.tval = h->tval;
         w.tbase = h->ltbase[j]; w.tcap = h->ltcap[j];
@@ -833,7 +837,6 @@ int symbolic_learned(spgemm_handle *h, const Operands &op, int64_t mrows, int64_
     CK(cudaMemcpyAsync(h_fb, L.fb, sizeof(unsigned long long) * kFbCounters, cudaMemcpyDeviceToHost, s));
     if ((rc = read_counters(h))) return rc;
     h->b_unsorted = (h->h_cnt[1].flags & 1ull) != 0;
-    h->b_distinct = false;
     *nnz_out = static_cast<int64_t>(h->h_cnt[1].total);
     h->lstats[0] = 0;
     for (int j = 0; j < last; ++j) h->lstats[0] += h->lsize[j];
@@ -1085,11 +1088,11 @@ int spgemm_symbolic(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_csr_i
     // cell index of B's long rows for kernels that cover rows in several
     // column windows (built here, used by both phases; the symbolic kernel
     // checks on the device that B is sorted)
-    if (h->split_on) {
+    if (h->split_on || h->mode == SPGEMM_MODE_LEARNED) {
         if (note(launch_sorted_check(op, B->rows, B->nnz, d_counters(h, 1), h->sm_count * 4, h->stream)) !=
             cudaSuccess)
             return fail(SPGEMM_ERR_CUDA);
-        if ((rc = build_bindex(h, op, B))) return fail(rc);
+        if (h->split_on && (rc = build_bindex(h, op, B))) return fail(rc);
     }
     if (h->mode == SPGEMM_MODE_LEARNED) {
         // the one-phase kernels multiply during this call: they read values
