@@ -477,6 +477,113 @@ __device__ __forceinline__ void block_row_walk(const Operands &op, int64_t p0, i
 
 namespace ops {
 
+// Asynchronous global -> shared copies of 4 and 8 bytes (cp.async, cached
+// in L1), their commit groups and waits. Each thread waits for its own
+// copies only.
+__device__ __forceinline__ void cp_async_4(void *sdst, const void *gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     static_cast<unsigned>(__cvta_generic_to_shared(sdst))),
+                 "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void *sdst, const void *gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                     static_cast<unsigned>(__cvta_generic_to_shared(sdst))),
+                 "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// B pieces a row group keeps in flight in group_row_walk_staged.
+constexpr int kStage = 3;
+
+// Row walk for a row group of TPR <= 32 lanes that takes one B row per step
+// in pieces of TPR entries (lane l: entry l of the piece) and stages B's
+// columns and values in shared memory with cp.async, kStage - 1 pieces
+// ahead of the one being added, so that the loads of the next B rows overlap
+// the hash updates of the current one. scol / sval: the group's
+// kStage * TPR slots (slot k of lane l at k * TPR + l); a lane reads only
+// the slots it copied itself. The group synchronises after every piece and
+// every lane runs the same trip counts, as in group_row_walk with SYNC: a
+// caller whose pieces hold distinct columns may update its table without
+// atomics. The pipeline runs within one chunk of TPR A entries (the A data
+// of a chunk sit one entry per lane) and drains at its end.
+template <int TPR, typename F>
+__device__ __forceinline__ void group_row_walk_staged(const Operands &op, int64_t p0, int64_t p1, int *scol,
+                                                      double *sval, F &&f) {
+    static_assert(TPR <= 32, "group walk is for sub-warp row groups");
+    const unsigned gm = group_mask<TPR>();
+    const int lg = threadIdx.x % TPR;
+    const int gbase = (threadIdx.x & 31) - lg;     // first lane of this group in the warp
+    const int64_t n = p1 - p0;
+    for (int64_t c = 0; c < n; c += TPR) {
+        const int cnt = static_cast<int>(n - c < TPR ? n - c : TPR);
+        long long my_q0 = 0;
+        int my_len = 0;
+        double my_a = 0.0;
+        if (lg < cnt) {
+            const int k = __ldg(op.acol + p0 + c + lg);
+            my_q0 = ld_rpt(op.brpt, op.b64, k);
+            my_len = static_cast<int>(ld_rpt(op.brpt, op.b64, k + 1) - my_q0);
+            my_a = __ldg(op.aval + p0 + c + lg);
+        }
+        // first non-empty entry at or after e (TPR: none); uniform over the group
+        auto next_entry = [&](int e, long long &q0, int &len) {
+            for (; e < TPR; ++e) {
+                len = __shfl_sync(gm, my_len, gbase + e);
+                if (len > 0) {
+                    q0 = __shfl_sync(gm, my_q0, gbase + e);
+                    return e;
+                }
+            }
+            return TPR;
+        };
+        // issue cursor: the next piece to copy
+        long long iq0 = 0;
+        int ilen = 0, ioff = 0;
+        int ie = next_entry(0, iq0, ilen);
+        auto issue = [&](int slot) {
+            if (ie < TPR) {
+                const int o = ioff + lg;
+                if (o < ilen) {
+                    cp_async_4(scol + slot * TPR + lg, op.bcol + iq0 + o);
+                    cp_async_8(sval + slot * TPR + lg, op.bval + iq0 + o);
+                }
+                ioff += TPR;
+                if (ioff >= ilen) {
+                    ioff = 0;
+                    ie = next_entry(ie + 1, iq0, ilen);
+                }
+            }
+            cp_async_commit();   // one group per slot, empty past the chunk's last piece
+        };
+#pragma unroll
+        for (int k = 0; k < kStage - 1; ++k) issue(k);
+        // processing cursor: the piece whose copies are the oldest group
+        long long pq0 = 0;
+        int plen = 0, poff = 0, slot = 0;
+        int pe = next_entry(0, pq0, plen);
+        while (pe < TPR) {   // uniform over the group
+            issue(slot == 0 ? kStage - 1 : slot - 1);
+            cp_async_wait<kStage - 1>();
+            const double a = __shfl_sync(gm, my_a, gbase + pe);
+            if (poff + lg < plen) f(scol[slot * TPR + lg], a, sval[slot * TPR + lg]);
+            __syncwarp(gm);
+            poff += TPR;
+            if (poff >= plen) {
+                poff = 0;
+                pe = next_entry(pe + 1, pq0, plen);
+            }
+            slot = slot + 1 == kStage ? 0 : slot + 1;
+        }
+        cp_async_wait<0>();   // only empty groups remain; slots are free for the next chunk
+    }
+}
+
 // Row walk for row groups of TPR <= 32 lanes (a slice of one warp). The
 // group loads TPR A entries at once into registers (one per lane), then its
 // sub-groups of S lanes take entries round-robin and read each B row in

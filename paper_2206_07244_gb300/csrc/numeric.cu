@@ -209,8 +209,16 @@ num_hash_kernel(Operands op, BinWork w) {
             if (!num_insert<T, MULTI>(tk, tv, key, a, b)) failed = true;
         });
     } else if (!MULTI && w.distinct && S == TPR) {
-        // one B row per step, its columns distinct: values without atomics
-        group_row_walk<TPR, true, true>(op, p0, p1, S, [&](int key, double a, double b) {
+        // one B row per step, its columns distinct: values without atomics,
+        // B's entries staged in shared memory by cp.async (after the tables:
+        // kStage * TPR values, then as many columns, per row group)
+        double *sv = reinterpret_cast<double *>(smem_raw + (sizeof(int) + sizeof(double)) * (size_t)RPB * T) +
+                     static_cast<size_t>(g) * kStage * TPR;
+        int *sc = reinterpret_cast<int *>(reinterpret_cast<double *>(smem_raw +
+                                                                      (sizeof(int) + sizeof(double)) * (size_t)RPB * T) +
+                                          static_cast<size_t>(RPB) * kStage * TPR) +
+                  static_cast<size_t>(g) * kStage * TPR;
+        group_row_walk_staged<TPR>(op, p0, p1, sc, sv, [&](int key, double a, double b) {
             if (!num_insert_owned<T>(tk, tv, key, a, b)) failed = true;
         });
     } else {
@@ -787,10 +795,12 @@ constexpr long long pow2_floor(long long t) {
     return p;
 }
 
+// Row groups of a warp or less also get kStage B-piece slots per lane for
+// the staged walk (12 bytes each).
 #define NUM_ENTRY(TPR, BLOCK, T)                                                         \
     {{TPR, BLOCK, T, pow2_floor(T), 0,                                                   \
       (sizeof(int) + sizeof(double)) * (BLOCK / TPR) * (size_t)T +                       \
-          (TPR > 32 ? sizeof(WalkScratch) : 0)},                                         \
+          (TPR > 32 ? sizeof(WalkScratch) : (sizeof(int) + sizeof(double)) * kStage * (size_t)BLOCK)}, \
      &num_hash_kernel<TPR, BLOCK, T>},
 
 static NumEntry g_num[] = {NUM_TABLE(NUM_ENTRY)};
