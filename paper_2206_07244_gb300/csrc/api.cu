@@ -1518,18 +1518,25 @@ static int multiply_host(spgemm_handle *h, const spgemm_csr_in *A, const spgemm_
             release();
             return SPGEMM_ERR_CUDA;
         }
-        long double total = 0;
-        for (int64_t v : np) total += (long double)v;
+        // integer sums and double ratios: long double is a software type on
+        // some hosts (128-bit on aarch64), far too slow for a loop over rows
+        int64_t total = 0;
+        for (int64_t v : np) total += v;
         // about 1.5e9 products per slab, and at least one slab per 8 chunks
         // of C at the n_prod upper bound (12 bytes per entry)
-        const long double by_work = total / 1.5e9L;
-        const long double by_copy = 12.0L * total / (8.0L * (long double)chunk_bytes);
-        const int S = static_cast<int>(std::min<long double>(64, std::max<long double>(1, std::max(by_work, by_copy))));
+        const double by_work = static_cast<double>(total) / 1.5e9;
+        const double by_copy = 12.0 * static_cast<double>(total) / (8.0 * static_cast<double>(chunk_bytes));
+        const int S = static_cast<int>(std::min(64.0, std::max(1.0, std::max(by_work, by_copy))));
         cut.assign(1, 0);
-        long double acc = 0;
+        // cut c (1 <= c < S) at the first row where the prefix reaches c / S of the total
+        int64_t acc = 0;
+        double next = static_cast<double>(total) / S;
         for (int64_t r = 0; r < M; ++r) {
-            acc += (long double)np[(size_t)r];
-            if ((int)cut.size() < S && acc >= total * (long double)cut.size() / S) cut.push_back(r + 1);
+            acc += np[(size_t)r];
+            if ((int)cut.size() < S && static_cast<double>(acc) >= next) {
+                cut.push_back(r + 1);
+                next = static_cast<double>(total) * static_cast<double>(cut.size()) / S;
+            }
         }
         if (cut.back() != M) cut.push_back(M);
         dev_free(h, d_np);
