@@ -158,9 +158,13 @@ __device__ __forceinline__ void warp_sort_store(const int *tk, const double *tv,
 }
 
 // Minimum resident blocks: enough for 2048 threads per SM (<= 32 registers
-// per thread, Sec. 5.6) unless the table is so large that one block fills
-// the SM's shared memory anyway; warp-per-row kernels that sort in registers
-// get 1536 threads per SM (42 registers) so the sort does not spill.
+// per thread, Sec. 5.6) for sub-warp row groups, unless the table is so
+// large that one block fills the SM's shared memory anyway. Kernels whose
+// walks and sorts spill at 32 registers get fewer threads and more
+// registers: warp-per-row kernels that sort in registers 1280 threads (48
+// registers; 27-point stencil 128^3: 10.64 -> 9.72 ms against 1536 threads),
+// block-per-row kernels 1536 (40 registers; block-diagonal n = 2^20:
+// 12.43 -> 10.44 ms against 2048).
 // ONE_PHASE (learned sizing): the row's size is not known; the table was
 // chosen from a prediction. A probe that finds no free slot, or more keys
 // than the table can sort in place, marks the row as mispredicted: it is
@@ -168,7 +172,7 @@ __device__ __forceinline__ void warp_sort_store(const int *tk, const double *tv,
 // size goes to C.rpt and its sorted entries to its temporary slot.
 template <int TPR, int BLOCK, int T, bool ONE_PHASE = false, bool MULTI = false>
 __global__ void __launch_bounds__(BLOCK, (T * 12 * (BLOCK / TPR) > 110 * 1024) ? 1
-                                         : ((TPR == 32 && T <= 256) ? 1536 : 2048) / BLOCK)
+                                         : ((TPR == 32 && T <= 256) ? 1280 : (TPR > 32 ? 1536 : 2048)) / BLOCK)
 num_hash_kernel(Operands op, BinWork w) {
     constexpr int RPB = BLOCK / TPR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
